@@ -1,0 +1,209 @@
+/*
+ * pyronn.h — C ABI of the GB300 (sm_103a) CT projector library (libpyronn.so).
+ *
+ * Operators of "An update to PYRO-NN" (Schneider et al.):
+ *   - the ray-driven forward projector A (Sec. 2.1: a ray per detector pixel, absorption
+ *     accumulated along its path),
+ *   - its exact transpose A^T (Sec. 2.2: "forward-projection operator A, with its adjoint"),
+ *   - the voxel-driven back-projector (Sec. 2.1: each voxel projected onto the detector,
+ *     detector values accumulated),
+ * for 2D parallel, 2D fan and 3D cone-beam geometries (Sec. 2.1), with each view described by a
+ * projection matrix so that calibrated matrices and arbitrary trajectories work (Sec. 2.1 last
+ * sentence, Sec. 2.4 "Flexible Trajectory Modeling").
+ *
+ * Discretisation (the paper gives the operators in prose only; these are the library's
+ * definitions, implemented identically by every kernel):
+ *   voxel (i, j, k) of an (Nz, Ny, Nx) volume with spacing (sz, sy, sx) and centre offset
+ *   (oz, oy, ox) sits at world ((i - (Nx-1)/2) sx + ox, (j - (Ny-1)/2) sy + oy, (k - (Nz-1)/2) sz + oz) mm;
+ *   ray r is sampled at t_k = (k + 1/2) dt (k integer, dt in mm, default half the smallest voxel
+ *   spacing) measured from its point closest to the volume centre; the volume is the
+ *   trilinear (2D: bilinear) hat-function interpolant I, zero outside the grid;
+ *     FP:      p_r = dt * sum_k I(c_r + t_k d_r)
+ *     adjoint: (A^T y)_v = sum_r y_r dt sum_k prod_axes hat(q(r, k) - v)
+ *     BP:      b_v = sum_views omega * (bilinear, zero-padded detector value at the projection of v),
+ *              omega = 1 or 1 / w^2, w the depth ratio of v between source and detector plane.
+ *
+ * Memory layout (row-major, contiguous, owned by the caller, device memory unless stated):
+ *   volume    [batch][Nz][Ny][Nx]   (2D: Nz = 1)
+ *   sinogram  [batch][V][Nv][Nu]    (2D: Nv = 1)
+ * Element type: PYRONN_F32, PYRONN_BF16 or PYRONN_F16 storage; all arithmetic is FP32.
+ * Buffers must be 16-byte aligned.
+ *
+ * Errors: every call returns PYRONN_OK (0) or a negative pyronn_status; pyronn_last_error()
+ * returns a message for the calling thread. Calls never abort and never trap on the device.
+ * Operator calls are asynchronous on the given stream (a cudaStream_t passed as void*, NULL for
+ * the legacy default stream) and never synchronise, except the *_host variants.
+ * The first operator call of a geometry on a device uploads its per-view tables with a
+ * synchronous copy; make that call before capturing a CUDA graph.
+ */
+#ifndef PYRONN_H
+#define PYRONN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PYRONN_API __attribute__((visibility("default")))
+#else
+#define PYRONN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pyronn_geom *pyronn_geom_t;
+
+typedef enum {
+    PYRONN_OK = 0,
+    PYRONN_INVALID_ARG = -1,
+    PYRONN_UNSUPPORTED_DTYPE = -2,
+    PYRONN_MISALIGNED = -3,
+    PYRONN_CUDA_ERROR = -4,
+    PYRONN_OOM = -5,
+    PYRONN_SINGULAR = -6,
+    PYRONN_DEVICE_CHECK_FAILED = -7
+} pyronn_status;
+
+typedef enum { PYRONN_F32 = 0, PYRONN_BF16 = 1, PYRONN_F16 = 2 } pyronn_dtype;
+
+typedef enum { PYRONN_BP_PLAIN = 0, PYRONN_BP_INV_W2 = 1 } pyronn_bp_weight;
+
+/* Volume description: the paper's volume_shape / volume_spacing (Listing 1), numpy (z, y, x)
+ * order. ndim = 2 describes an image: shape[0] must be 1, spacing[0] and offset[0] are ignored. */
+typedef struct {
+    int ndim;
+    int shape[3];        /* (Nz, Ny, Nx) */
+    double spacing[3];   /* (sz, sy, sx) mm */
+    double offset[3];    /* (oz, oy, ox) world position of the volume centre, mm */
+} pyronn_vol_desc;
+
+/* Detector description: the paper's detector_shape / detector_spacing (Listing 1), (rows, cols).
+ * For 2D geometries shape[0] must be 1. offset shifts the detector centre along (ev, eu). */
+typedef struct {
+    int shape[2];        /* (Nv, Nu) */
+    double spacing[2];   /* (dv, du) mm */
+    double offset[2];    /* (ov, ou) mm */
+} pyronn_det_desc;
+
+/* ------------------------------------------------------------------------------------------
+ * Geometry (host-side; FP64). The handle owns its host tables, its per-device view tables and
+ * any scratch it needs; release it with pyronn_geom_destroy. Creation needs no GPU.
+ * ---------------------------------------------------------------------------------------- */
+
+/* 2D parallel beam (Sec. 2.1). View n at angle t = n * angular_range / n_views; rays run along
+ * -(cos t, sin t); bin u lies at (u - (Nu-1)/2) du + ou along (-sin t, cos t). */
+PYRONN_API int pyronn_geom_create_parallel2d(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_views,
+                                  double angular_range, pyronn_geom_t *out);
+
+/* 2D fan beam (Sec. 2.1): the z = 0 plane of the circular orbit below (sid = source-isocentre,
+ * sdd = source-detector distance, Listing 1). */
+PYRONN_API int pyronn_geom_create_fan2d(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_views,
+                             double angular_range, double sid, double sdd, pyronn_geom_t *out);
+
+/* 3D cone beam on a circular (helical_pitch_mm = 0) or helical orbit (Listing 1 parameters:
+ * number_of_projections, angular_range, sdd, sid). View n at angle t = n * angular_range / n_views:
+ * source sid (cos t, sin t, z_n), detector centre -(sdd - sid) (cos t, sin t, 0) + (0, 0, z_n),
+ * eu = (-sin t, cos t, 0), ev = (0, 0, 1), z_n = pitch (n - (V-1)/2) (angular_range / V) / (2 pi).
+ * The per-view matrices are built as in Sec. 2.4 (from source and detector positions). */
+PYRONN_API int pyronn_geom_create_cone_circular(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_views,
+                                     double angular_range, double sid, double sdd, double helical_pitch_mm,
+                                     pyronn_geom_t *out);
+
+/* 3D cone beam from source / detector positions and detector directions (Sec. 2.4, after
+ * Graetz): src, det_centre, eu, ev are n_views x 3 world-mm arrays (eu, ev need not be unit:
+ * they are normalised). P = M^-1 [I | -S] with M = [du eu | dv ev | D0 - S] and D0 the centre of
+ * pixel (0, 0). Returns PYRONN_SINGULAR if a view's M is singular. */
+PYRONN_API int pyronn_geom_create_from_positions(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_views,
+                                      const double *src, const double *det_centre, const double *eu,
+                                      const double *ev, pyronn_geom_t *out);
+
+/* 3D cone beam from calibrated projection matrices (Sec. 2.1, Sec. 2.4): P is n_views x 3 x 4
+ * row-major, mapping world (x, y, z, 1) mm to (u w, v w, w) with (u, v) pixel indices. Each
+ * matrix is rescaled so that inv(P[:, :3]) has a first column of length du and w > 0 at the
+ * volume centre. Returns PYRONN_SINGULAR if P[:, :3] is singular or w vanishes there. */
+PYRONN_API int pyronn_geom_create_cone_matrices(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_views,
+                                     const double *P, pyronn_geom_t *out);
+
+/* 2D fan beam from 2 x 3 matrices (n_views x 2 x 3, world (x, y, 1) -> (u w, w)), or 2D parallel
+ * beam when every matrix's last row is (0, 0, 1) (u = P[0] . (x, y, 1)). Normalised like the
+ * 3D matrices (|inv(P[:, :2]) column 0| = du, w > 0 at the image centre). */
+PYRONN_API int pyronn_geom_create_matrices2d(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_views,
+                                  const double *P, pyronn_geom_t *out);
+
+PYRONN_API int pyronn_geom_destroy(pyronn_geom_t g);
+
+/* Sampling step along rays in mm (> 0). Default: half the smallest voxel spacing. */
+PYRONN_API int pyronn_geom_set_step(pyronn_geom_t g, double dt_mm);
+PYRONN_API int pyronn_geom_get_step(pyronn_geom_t g, double *dt_mm);
+
+/* Number of views; geometry kind (0 parallel, 1 perspective). */
+PYRONN_API int pyronn_geom_info(pyronn_geom_t g, int *n_views, int *kind, int *ndim);
+
+/* Copy out the normalised per-view matrices: n_views x 12 doubles. Perspective views: P (3 x 4).
+ * Parallel views: Dc[3], eu[3], ev[3], d[3] (detector centre, axes, ray direction). */
+PYRONN_API int pyronn_geom_get_views(pyronn_geom_t g, double *out);
+
+/* Exact number of (ray, sample) pairs whose sample lies inside the open support box (-1, N_a) on
+ * every axis, summed over all views (FP64 host computation, multithreaded, cached). This is the
+ * work unit of the forward projector's throughput. */
+PYRONN_API int pyronn_geom_count_samples(pyronn_geom_t g, int64_t *total);
+
+/* ------------------------------------------------------------------------------------------
+ * Operators (device buffers, asynchronous on `stream`).
+ * ---------------------------------------------------------------------------------------- */
+
+/* Forward projection (Sec. 2.1 ray-driven; operator A of Sec. 2.2): sino = A vol, overwriting
+ * sino. */
+PYRONN_API int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, void *stream);
+
+/* Matched adjoint (operator A^T of Sec. 2.2, the exact transpose of pyronn_fp):
+ * vol = A^T sino, overwriting vol. For BF16/F16 storage the sum is formed in FP32 in a
+ * geometry-owned scratch buffer (allocated on first use) and converted once at the end. */
+PYRONN_API int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, void *stream);
+
+/* Voxel-driven back-projection (Sec. 2.1): vol = BP sino, overwriting vol; weight is a
+ * pyronn_bp_weight. Not the transpose of pyronn_fp. */
+PYRONN_API int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, int weight, void *stream);
+
+/* Exact transpose of pyronn_bp (the gradient of the voxel-driven back-projector with respect to
+ * its sinogram, Sec. 2.1 "analytical gradients for all operators"): sino = BP^T vol, overwriting
+ * sino. Each voxel spreads its value times omega over the four detector pixels around its
+ * projection with the bilinear weights. BF16/F16 storage accumulates in FP32 scratch. */
+PYRONN_API int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, int weight,
+                                   void *stream);
+
+/* Host-buffer variants: copy the input from host memory (pinned for best speed) into device
+ * buffers owned by the geometry (allocated on first use), run the operator on `stream`, copy
+ * the result back and synchronise the stream. */
+PYRONN_API int pyronn_fp_host(pyronn_geom_t g, const void *vol_host, void *sino_host, int dtype, int batch, void *stream);
+PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void *vol_host, int dtype, int batch,
+                        void *stream);
+
+/* Kernel variant of an operator, for tests and tuning: op 0 = forward projection
+ * (variant 0 automatic, 1 one-thread-per-ray read-only-cache kernel, 2 slab-staged shared-memory
+ * kernel; 2 falls back to 1 when the staged box cannot fit in shared memory). All variants
+ * compute the same operator. */
+PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
+
+/* ------------------------------------------------------------------------------------------
+ * Diagnostics.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Read (and optionally reset) the geometry's device diagnostic counters, 8 ints: [0] samples of
+ * the slab-staged projector that fell outside their staged box and were read from global memory
+ * instead, [1] rays sampled outside the slab march (nearly parallel to the slabs), [2] slabs whose
+ * box exceeded shared memory. Synchronous (device-wide copy). All zero is the expected state. */
+PYRONN_API int pyronn_geom_read_flags(pyronn_geom_t g, int *out, int reset);
+
+/* Message describing the last error of the calling thread ("" if none). */
+PYRONN_API const char *pyronn_last_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+PYRONN_API int pyronn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYRONN_H */

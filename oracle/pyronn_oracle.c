@@ -20,7 +20,8 @@
  *   - FP:  p_r = dt * sum_k I(c_r + t_k d_r);
  *   - A^T: (A^T y)_v = sum_r y_r dt sum_k prod_a hat(q_a(r,k) - v_a)   (exact transpose of FP);
  *   - BP:  b_v = sum_views omega * sum_{u',v'} q[v',u'] hat(u - u') hat(v - v'), with (u, v, w)
- *          the projection of the voxel centre, omega = 1 or 1/w^2.
+ *          the projection of the voxel centre, omega = 1 or 1/w^2; views with w <= 0 (voxel at or
+ *          behind the source plane) contribute nothing.
  *
  * Parity status: every function here is pinned by tests that do not reuse this code
  * (closed forms, invariants, brute force on tiny grids); see tests/test_oracle_pins.py.
@@ -368,6 +369,8 @@ static double bp_one(const og_t *g, const double *sino, int weight_mode, long vo
     for (int n = 0; n < g->n_views; ++n) {
         double u, v, w;
         project(g, n, X, &u, &v, &w);
+        /* reading: a voxel at or behind the source plane (w <= 0) receives nothing from the view */
+        if (g->kind == 1 && !(w > 0.0)) continue;
         long u0 = (long)floor(u), v0 = (long)floor(v);
         const double *q = sino + (size_t)n * g->nu * g->nv;
         double s = 0.0;

@@ -1,0 +1,176 @@
+// C ABI of the operators: argument validation, lazy device set-up and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "pyronn_internal.h"
+
+using namespace pyronn;
+
+namespace {
+
+int check_ptr(const void *p, const char *what) {
+    if (!p) return set_error(PYRONN_INVALID_ARG, "%s is null", what);
+    if (((uintptr_t)p) & 15u) return set_error(PYRONN_MISALIGNED, "%s is not 16-byte aligned", what);
+    return PYRONN_OK;
+}
+
+int common_checks(pyronn_geom_t g, int dtype, int batch) {
+    if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
+    if (dtype_size(dtype) == 0) return set_error(PYRONN_UNSUPPORTED_DTYPE, "unsupported dtype %d", dtype);
+    if (batch < 1) return set_error(PYRONN_INVALID_ARG, "batch must be >= 1 (got %d)", batch);
+    long long nvox = (long long)g->nx * g->ny * g->nz;
+    long long nsino = (long long)g->nu * g->nv * g->n_views;
+    if (nvox >= (1LL << 31) || (long long)g->nu * g->nv >= (1LL << 31))
+        return set_error(PYRONN_INVALID_ARG, "volume or detector too large for 32-bit in-volume indexing");
+    if (nsino * batch <= 0 || nvox * batch <= 0) return set_error(PYRONN_INVALID_ARG, "empty operand");
+    return ensure_device(g);
+}
+
+int cuda_rc(int e, const char *what) {
+    if (e == 0) return PYRONN_OK;
+    return set_error(PYRONN_CUDA_ERROR, "%s: %s", what, cudaGetErrorString((cudaError_t)e));
+}
+
+int ensure_scratch(pyronn_geom_t g, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->scratch_bytes >= bytes) return PYRONN_OK;
+    if (g->d_scratch) cudaFree(g->d_scratch);
+    g->d_scratch = nullptr;
+    g->scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&g->d_scratch, bytes);
+    if (e != cudaSuccess) return set_error(PYRONN_OOM, "scratch allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    g->scratch_bytes = bytes;
+    return PYRONN_OK;
+}
+
+int ensure_stage(pyronn_geom_t g, size_t in_bytes, size_t out_bytes) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    cudaError_t e = cudaSuccess;
+    if (g->stage_in_bytes < in_bytes) {
+        cudaFree(g->d_stage_in);
+        g->d_stage_in = nullptr;
+        g->stage_in_bytes = 0;
+        e = cudaMalloc(&g->d_stage_in, in_bytes);
+        if (e != cudaSuccess) return set_error(PYRONN_OOM, "staging allocation: %s", cudaGetErrorString(e));
+        g->stage_in_bytes = in_bytes;
+    }
+    if (g->stage_out_bytes < out_bytes) {
+        cudaFree(g->d_stage_out);
+        g->d_stage_out = nullptr;
+        g->stage_out_bytes = 0;
+        e = cudaMalloc(&g->d_stage_out, out_bytes);
+        if (e != cudaSuccess) return set_error(PYRONN_OOM, "staging allocation: %s", cudaGetErrorString(e));
+        g->stage_out_bytes = out_bytes;
+    }
+    return PYRONN_OK;
+}
+
+const FpSlabCfg &fp_cfg(pyronn_geom_t g) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (!g->fp_cfg_ready) {
+        g->fp_cfg = choose_fp_slab_cfg(g);
+        g->fp_cfg_ready = 1;
+    }
+    return g->fp_cfg;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
+    OpParams p = make_params(g, batch);
+    if (g->fp_variant == 1)
+        return cuda_rc(launch_fp_direct(p, vol, sino, dtype, stream), "forward projection launch");
+    return cuda_rc(launch_fp(p, fp_cfg(g), vol, sino, dtype, stream), "forward projection launch");
+}
+
+int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant) {
+    clear_error();
+    if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
+    if (op != 0) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
+    if (variant < 0 || variant > 2) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
+    g->fp_variant = variant;
+    return PYRONN_OK;
+}
+
+int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
+    OpParams p = make_params(g, batch);
+    float *acc = nullptr;
+    if (dtype != PYRONN_F32) {
+        if ((rc = ensure_scratch(g, sizeof(float) * (size_t)p.vol_elems * batch))) return rc;
+        acc = (float *)g->d_scratch;
+    }
+    return cuda_rc(launch_adjoint(p, sino, vol, acc, dtype, stream), "adjoint launch");
+}
+
+int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, int weight, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
+    if (weight != PYRONN_BP_PLAIN && weight != PYRONN_BP_INV_W2)
+        return set_error(PYRONN_INVALID_ARG, "unknown back-projection weight %d", weight);
+    OpParams p = make_params(g, batch);
+    p.weight = weight;
+    return cuda_rc(launch_bp(p, sino, vol, dtype, stream), "back-projection launch");
+}
+
+int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, int weight,
+                        void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
+    if (weight != PYRONN_BP_PLAIN && weight != PYRONN_BP_INV_W2)
+        return set_error(PYRONN_INVALID_ARG, "unknown back-projection weight %d", weight);
+    OpParams p = make_params(g, batch);
+    p.weight = weight;
+    float *acc = nullptr;
+    if (dtype != PYRONN_F32) {
+        if ((rc = ensure_scratch(g, sizeof(float) * (size_t)p.sino_elems * batch))) return rc;
+        acc = (float *)g->d_scratch;
+    }
+    return cuda_rc(launch_bp_transpose(p, vol, sino, acc, dtype, stream), "back-projection transpose launch");
+}
+
+static int host_op(pyronn_geom_t g, const void *in_host, void *out_host, int dtype, int batch, void *stream, int fp) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if (!in_host || !out_host) return set_error(PYRONN_INVALID_ARG, "null host buffer");
+    size_t es = dtype_size(dtype);
+    size_t vol_bytes = es * (size_t)g->nx * g->ny * g->nz * batch;
+    size_t sino_bytes = es * (size_t)g->nu * g->nv * g->n_views * batch;
+    size_t in_bytes = fp ? vol_bytes : sino_bytes, out_bytes = fp ? sino_bytes : vol_bytes;
+    if ((rc = ensure_stage(g, in_bytes, out_bytes))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(g->d_stage_in, in_host, in_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_rc((int)e, "host-to-device copy");
+    rc = fp ? pyronn_fp(g, g->d_stage_in, g->d_stage_out, dtype, batch, stream)
+            : pyronn_adjoint(g, g->d_stage_in, g->d_stage_out, dtype, batch, stream);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(out_host, g->d_stage_out, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_rc((int)e, "device-to-host copy");
+    return cuda_rc((int)cudaStreamSynchronize(st), "stream synchronise");
+}
+
+int pyronn_fp_host(pyronn_geom_t g, const void *vol_host, void *sino_host, int dtype, int batch, void *stream) {
+    return host_op(g, vol_host, sino_host, dtype, batch, stream, 1);
+}
+
+int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void *vol_host, int dtype, int batch, void *stream) {
+    return host_op(g, sino_host, vol_host, dtype, batch, stream, 0);
+}
+
+}  // extern "C"

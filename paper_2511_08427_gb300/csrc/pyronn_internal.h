@@ -1,0 +1,130 @@
+// Internal declarations shared by the host geometry code, the C ABI and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pyronn.h"
+
+namespace pyronn {
+
+// ---------------------------------------------------------------------------------------------
+// Device-side per-view records (FP32), built once per geometry on the host in FP64.
+// ---------------------------------------------------------------------------------------------
+
+// Ray family of one view, in world mm relative to the volume centre C:
+//   reference point  Y(u, v) = R0 + u Ru + v Rv   (a point on the ray of pixel (u, v))
+//   direction        D(u, v) = B0 + u Bu + v Bv   (unnormalised)
+// Perspective views take Y on the plane through C parallel to the detector, so |Y| stays of the
+// order of the volume size and the closest-point construction loses no FP32 precision.
+struct FpRec {
+    float R0[3], Ru[3], Rv[3];
+    float B0[3], Bu[3], Bv[3];
+};
+
+// Projection of centred voxel indices (i - (Nx-1)/2, j - (Ny-1)/2, k - (Nz-1)/2, 1) to centred
+// detector coordinates times depth: (u_c w, v_c w, w); u = u_c + (Nu-1)/2. Row-major 3 x 4.
+struct BpRec {
+    float P[12];
+};
+
+struct VolDims {
+    int nx, ny, nz;
+    float hx, hy, hz;      // (N - 1) / 2
+    float isx, isy, isz;   // 1 / spacing (index units per mm)
+};
+
+struct DetDims {
+    int nu, nv;
+    float hu, hv;          // (N - 1) / 2
+};
+
+// Everything a kernel needs besides the data pointers.
+struct OpParams {
+    VolDims vol;
+    DetDims det;
+    int n_views;
+    int batch;
+    int perspective;       // 1: divide by w in BP; 0: affine (parallel) views
+    int weight;            // BP weight mode (pyronn_bp_weight)
+    float dt;              // sampling step, mm
+    const FpRec *fp;       // device, n_views records
+    const BpRec *bp;       // device, n_views records
+    long long vol_elems;   // elements per volume
+    long long sino_elems;  // elements per sinogram
+    int *flags;            // device diagnostic counters (geometry-owned, see pyronn_geom_read_flags)
+};
+
+// Diagnostic counters (device, per geometry).
+enum { FLAG_SLAB_OUT_OF_BOX = 0, FLAG_SLAB_DIRECT_RAY = 1, FLAG_SLAB_OVERFLOW = 2, N_FLAGS = 8 };
+
+// Launch configuration of the slab-staged forward projector (chosen per geometry).
+struct FpSlabCfg {
+    int tu, tv;            // detector tile (rays per CTA = tu * tv)
+    int depth;             // march slab depth in voxels
+    int guard;             // extra staged planes on each side of a slab
+    int smem_floats;       // staged box capacity
+    int valid;             // 0: use the direct kernel
+};
+
+}  // namespace pyronn
+
+// ---------------------------------------------------------------------------------------------
+// Geometry handle.
+// ---------------------------------------------------------------------------------------------
+struct pyronn_geom {
+    int kind = 1;                  // 0 parallel, 1 perspective
+    int ndim = 3;
+    int nx = 0, ny = 0, nz = 0;
+    double sx = 1, sy = 1, sz = 1;
+    double ox = 0, oy = 0, oz = 0;
+    int nu = 0, nv = 0;
+    double du = 1, dv = 1, ou = 0, ov = 0;
+    int n_views = 0;
+    double dt = 0;
+    std::vector<double> views;     // n_views x 12: P (perspective) or Dc, eu, ev, d (parallel)
+    std::vector<pyronn::FpRec> fp_rec;
+    std::vector<pyronn::BpRec> bp_rec;
+
+    // device state (one device per handle)
+    std::mutex mu;
+    int device = -1;
+    pyronn::FpRec *d_fp = nullptr;
+    pyronn::BpRec *d_bp = nullptr;
+    int *d_flags = nullptr;
+    void *d_scratch = nullptr;     // FP32 accumulation buffer for reduced-precision adjoints
+    size_t scratch_bytes = 0;
+    void *d_stage_in = nullptr;    // device buffers of the host-buffer entry points
+    void *d_stage_out = nullptr;
+    size_t stage_in_bytes = 0, stage_out_bytes = 0;
+
+    int64_t sample_count = -1;     // cached pyronn_geom_count_samples
+    pyronn::FpSlabCfg fp_cfg{};    // 0-initialised: chosen on first use
+    int fp_cfg_ready = 0;
+    int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged
+};
+
+namespace pyronn {
+
+// error reporting (thread-local message)
+int set_error(int code, const char *fmt, ...);
+void clear_error();
+
+// geometry helpers (geometry.cpp)
+int finalize_geometry(pyronn_geom *g);          // build FP32 tables from views
+int ensure_device(pyronn_geom *g);               // upload tables to the current device
+OpParams make_params(const pyronn_geom *g, int batch);
+FpSlabCfg choose_fp_slab_cfg(const pyronn_geom *g);
+
+// kernel launchers (return a cudaError_t as int)
+int launch_fp(const OpParams &p, const FpSlabCfg &cfg, const void *vol, void *sino, int dtype, void *stream);
+int launch_fp_direct(const OpParams &p, const void *vol, void *sino, int dtype, void *stream);
+int launch_adjoint(const OpParams &p, const void *sino, void *vol, float *acc32, int dtype, void *stream);
+int launch_bp(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
+int launch_bp_transpose(const OpParams &p, const void *vol, void *sino, float *acc32, int dtype, void *stream);
+
+size_t dtype_size(int dtype);
+
+}  // namespace pyronn

@@ -1,0 +1,130 @@
+"""CPU-side checks of the C ABI (no kernel launches): the library loads and exports every entry
+point that include/pyronn.h declares, the host geometry code matches the FP64 oracle's
+geometry, the sample count matches the oracle's count, and invalid arguments are rejected."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_08427_gb300 import _lib, inputs
+
+from cases import SMALL, Case
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2511_08427_gb300 import build
+    build.build()
+    return _lib.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "pyronn.h")).read()
+    return sorted(set(re.findall(r"PYRONN_API\s+(?:const\s+char\s*\*|int)\s*(pyronn_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    decl = declared_symbols()
+    assert len(decl) >= 20
+    for name in decl:
+        assert hasattr(L, name), name
+    # and the binding marshals exactly the declared set
+    assert sorted(_lib.exported_symbols()) == decl
+
+
+def test_version_and_error_string(L):
+    assert L.pyronn_version() >= 100
+    assert isinstance(L.pyronn_last_error(), bytes)
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
+def test_library_views_match_oracle(L, case: Case):
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    assert g.kind == og.kind
+    assert np.allclose(g.views(), og.views, rtol=1e-12, atol=1e-12)
+    assert abs(g.step - og.dt) < 1e-15
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
+def test_sample_count_matches_oracle(L, case: Case):
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    assert g.count_samples() == int(oracle.count_samples(og).sum())
+
+
+def test_matrices_paths_match_oracle(L):
+    from paper_2511_08427_gb300.operators import Geometry
+    vs, sp, ds, dsp = (10, 12, 14), (0.5, 0.6, 0.7), (9, 11), (0.8, 0.9)
+    og = oracle.cone_circular(vs, sp, ds, dsp, 7, 2 * math.pi, 70.0, 110.0)
+    scale = np.linspace(-3.0, 5.0, 7)
+    scale[scale == 0] = 1.0
+    g = Geometry.cone_from_matrices(vs, sp, ds, dsp, og.views * scale[:, None])
+    assert np.allclose(g.views(), og.views, rtol=1e-12, atol=1e-13)
+    # 2D fan from 2 x 3 matrices: the (u, w) rows of the 3D fan embedding
+    of = oracle.fan_circular((20, 22), (0.5, 0.5), 31, 1.0, 5, 2 * math.pi, 100.0, 150.0)
+    P2 = of.views.reshape(-1, 3, 4)[:, [0, 2], :][:, :, [0, 1, 3]] * 2.5
+    gf = Geometry.from_matrices2d((20, 22), (0.5, 0.5), 31, 1.0, P2)
+    assert gf.kind == 1
+    assert np.allclose(gf.views(), of.views, rtol=1e-12, atol=1e-13)
+    # 2D parallel from affine 2 x 3 matrices u = (X . eu) / du + (Nu - 1) / 2 - ou / du
+    op = oracle.parallel2d((20, 22), (0.5, 0.5), 31, 0.8, 6, math.pi, det_offset=0.25)
+    rows = []
+    for n in range(6):
+        eu = op.views[n, 3:5]
+        rows.append([[eu[0] / 0.8, eu[1] / 0.8, 15.0 - 0.25 / 0.8], [0.0, 0.0, 1.0]])
+    gp = Geometry.from_matrices2d((20, 22), (0.5, 0.5), 31, 0.8, np.array(rows))
+    assert gp.kind == 0
+    v = gp.views()
+    # same rays (origin line and direction up to sign) as the oracle's parallel geometry
+    for n in range(6):
+        eu, d = v[n, 3:6], v[n, 9:12]
+        assert np.allclose(eu, op.views[n, 3:6], atol=1e-12)
+        assert abs(abs(np.dot(d, op.views[n, 9:12])) - 1.0) < 1e-12
+        # the detector-centre offsets agree along eu
+        assert abs(np.dot(v[n, 0:3], eu) - (np.dot(op.views[n, 0:3], eu) + 0.25)) < 1e-12
+
+
+def test_positions_path_matches_oracle(L):
+    from paper_2511_08427_gb300.operators import Geometry
+    tr = inputs.jittered_circular_trajectory(8, 2 * math.pi, 750.0, 1200.0, 0.5, 0.2, seed=5)
+    vs, sp, ds, dsp = (16, 16, 16), (0.4, 0.4, 0.4), (12, 14), (0.4, 0.4)
+    g = Geometry.cone_from_positions(vs, sp, ds, dsp, tr.src, tr.det_centre, tr.eu, tr.ev)
+    og = oracle.cone_from_positions(vs, sp, ds, dsp, tr.src, tr.det_centre, tr.eu, tr.ev)
+    assert np.allclose(g.views(), og.views, rtol=1e-12, atol=1e-12)
+
+
+def test_invalid_arguments_are_rejected(L):
+    from paper_2511_08427_gb300.operators import Geometry
+    with pytest.raises(_lib.PyronnError) as e:
+        Geometry.cone_circular((0, 4, 4), (1, 1, 1), (4, 4), (1, 1), 3, 1.0, 10.0, 20.0)
+    assert e.value.code == -1
+    with pytest.raises(_lib.PyronnError):
+        Geometry.cone_circular((4, 4, 4), (1, 1, 1), (4, 4), (1, 1), 3, 1.0, 30.0, 20.0)   # sdd < sid
+    with pytest.raises(_lib.PyronnError) as e:
+        Geometry.cone_from_matrices((4, 4, 4), (1, 1, 1), (4, 4), (1, 1), np.zeros((2, 12)))
+    assert e.value.code == -6
+    g = Geometry.cone_circular((4, 4, 4), (1, 1, 1), (4, 4), (1, 1), 3, 1.0, 10.0, 20.0)
+    with pytest.raises(_lib.PyronnError):
+        g.step = -1.0
+    with pytest.raises(_lib.PyronnError):
+        g.set_variant(0, 7)
+    # operator calls validate before touching the device
+    assert L.pyronn_fp(g.handle, None, None, 0, 1, None) != 0
+    assert L.pyronn_fp(g.handle, ctypes.c_void_p(16), ctypes.c_void_p(32), 9, 1, None) == -2
+    assert L.pyronn_bp(None, None, None, 0, 1, 0, None) == -1
+    assert b"null" in L.pyronn_last_error()
+
+
+def test_step_changes_sample_count(L):
+    from paper_2511_08427_gb300.operators import Geometry
+    g = Geometry.parallel2d((8, 20), (1.0, 1.0), 5, 1.0, 1)
+    assert g.count_samples() == 5 * (2 * 20 + 2)     # closed form of the symmetric lattice
+    g.step = 0.25
+    assert g.count_samples() == 5 * (4 * 20 + 4)

@@ -1,0 +1,327 @@
+"""GPU parity: the CUDA operators (through the C ABI) against the FP64 oracle.
+
+Tolerances. FP32 storage: relative L2 <= 1e-5 per output tensor (the target the operators are
+held to); FP32 arithmetic with FP32 per-view geometry gives ~1e-7..1e-6 in practice. BF16 / FP16
+storage: the oracle is fed the same rounded inputs, so the remaining error is the output rounding
+(2^-9 relative for BF16, 2^-12 for FP16) plus FP32 arithmetic: rel-L2 <= 4e-3 (BF16) and
+<= 5e-4 (FP16). Dot-product (adjoint) test: |<Ax, y> - <x, A^T y>| <= 1e-6 |<Ax, y>| with the
+inner products accumulated in FP64 on the host.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_08427_gb300 import inputs
+
+from cases import CFG1, CFG2, CFG3, SMALL, Case, cfg_phantom, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float32: 1e-5, torch.bfloat16: 4e-3, torch.float16: 5e-4}
+
+
+@pytest.fixture(scope="module")
+def ops():
+    from paper_2511_08427_gb300 import build
+    build.build()
+    from paper_2511_08427_gb300 import operators
+    return operators
+
+
+DEV = "cuda:0"
+
+
+def to_dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV).to(dtype)
+
+
+def host(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def sino3(case: Case, s):
+    """Library 2D sinograms are [V, Nu]; the oracle's are [V, 1, Nu]."""
+    s = np.asarray(s)
+    return s.reshape(s.shape[0], 1, s.shape[1]) if case.ndim == 2 else s
+
+
+_oracle_cache = {}
+
+
+def oracle_fp(case, x):
+    key = ("fp", case.name, x.tobytes().__hash__())
+    if key not in _oracle_cache:
+        _oracle_cache[key] = oracle.fp(case.oracle_geometry(), x)
+    return _oracle_cache[key]
+
+
+# ------------------------------------------------------------------------------------------------
+# small cases: every geometry, every kernel variant, every storage type
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
+def test_fp_matches_oracle(ops, case, variant):
+    g = case.library_geometry()
+    g.set_variant(0, variant)
+    x = case.phantom()
+    p = host(ops.forward_project(to_dev(x), g))
+    assert rel_l2(sino3(case, p), oracle_fp(case, x)) <= 1e-5
+    assert g.read_flags()[:3] == [0, 0, 0]
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
+def test_adjoint_matches_oracle(ops, case):
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    y = inputs.gaussian(og.sino_shape, seed=22)
+    a = host(ops.adjoint(to_dev(y.reshape((og.n_views, -1)) if case.ndim == 2 else y), g))
+    ref = oracle.adjoint(og, y)
+    assert rel_l2(a.reshape(ref.shape), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("weight", [0, 1])
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
+def test_bp_matches_oracle(ops, case, weight):
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    q = inputs.uniform(og.sino_shape, seed=9)
+    b = host(ops.back_project(to_dev(q.reshape((og.n_views, -1)) if case.ndim == 2 else q), g, weight))
+    ref = oracle.bp(og, q, weight)
+    assert rel_l2(b.reshape(ref.shape), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
+def test_dot_product_adjoint_gpu(ops, case):
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    x = inputs.uniform(case.vol_shape3, seed=31).reshape(
+        case.params["vol_shape"] if case.ndim == 2 else case.vol_shape3)
+    y = inputs.gaussian(og.sino_shape, seed=32).reshape((og.n_views, -1) if case.ndim == 2 else og.sino_shape)
+    ax = host(ops.forward_project(to_dev(x), g))
+    aty = host(ops.adjoint(to_dev(y), g))
+    lhs = float(np.vdot(ax.ravel(), y.astype(np.float64).ravel()))
+    rhs = float(np.vdot(x.astype(np.float64).ravel(), aty.ravel()))
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+@pytest.mark.parametrize("weight", [0, 1])
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
+def test_bp_transpose_against_oracle_bp(ops, case, weight):
+    """<BP q, x> (oracle BP, FP64) equals <q, BP^T x> (GPU transpose)."""
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    q = inputs.gaussian(og.sino_shape, seed=41)
+    x = inputs.uniform(og.vol_shape, seed=42)
+    xt = x.reshape(case.params["vol_shape"]) if case.ndim == 2 else x
+    bt = host(ops.back_project_transpose(to_dev(xt), g, weight))
+    lhs = float(np.vdot(oracle.bp(og, q, weight).ravel(), x.astype(np.float64).ravel()))
+    rhs = float(np.vdot(q.astype(np.float64).ravel(), bt.ravel()))
+    assert abs(lhs - rhs) <= 1e-6 * max(abs(lhs), 1e-30)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
+def test_reduced_precision_storage(ops, case, dtype):
+    """BF16 / FP16 storage with FP32 arithmetic; the oracle sees the same rounded inputs."""
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    x = case.phantom()
+    xd = to_dev(x, dtype)
+    xr = host(xd)
+    p = host(ops.forward_project(xd, g))
+    assert rel_l2(sino3(case, p), oracle.fp(og, xr)) <= TOL[dtype]
+    y = inputs.gaussian(og.sino_shape, seed=22)
+    yd = to_dev(y.reshape((og.n_views, -1)) if case.ndim == 2 else y, dtype)
+    a = host(ops.adjoint(yd, g))
+    ref = oracle.adjoint(og, host(yd).reshape(og.sino_shape))
+    assert rel_l2(a.reshape(ref.shape), ref) <= TOL[dtype]
+    b = host(ops.back_project(yd, g))
+    refb = oracle.bp(og, host(yd).reshape(og.sino_shape))
+    assert rel_l2(b.reshape(refb.shape), refb) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("case", SMALL[:3], ids=lambda c: c.name)
+def test_batch_equals_single_calls(ops, case):
+    g = case.library_geometry()
+    xs = np.stack([case.phantom(seed=s) for s in (1, 2, 3)])
+    pb = host(ops.forward_project(to_dev(xs), g))
+    for i in range(3):
+        assert np.array_equal(pb[i], host(ops.forward_project(to_dev(xs[i]), g)))
+    y = inputs.gaussian(pb.shape, seed=5)
+    ab = host(ops.adjoint(to_dev(y), g))
+    for i in range(3):
+        assert rel_l2(ab[i], host(ops.adjoint(to_dev(y[i]), g))) <= 1e-6
+
+
+def test_autograd_backward_is_matched_adjoint(ops):
+    case = SMALL[2]
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    x = to_dev(case.phantom()).requires_grad_(True)
+    p = ops.project(x, g)
+    yc = inputs.gaussian(tuple(p.shape), seed=22)
+    (p * to_dev(yc)).sum().backward()
+    assert rel_l2(host(x.grad), oracle.adjoint(og, yc)) <= 1e-5
+    # back-projector gradient is its exact transpose; projector-adjoint gradient is the projector
+    q = to_dev(inputs.uniform(tuple(p.shape), seed=3)).requires_grad_(True)
+    b = ops.backproject(q, g)
+    xc = to_dev(inputs.gaussian(tuple(b.shape), seed=4))
+    (b * xc).sum().backward()
+    assert torch.allclose(q.grad, ops.back_project_transpose(xc, g))
+    y2 = to_dev(yc).requires_grad_(True)
+    a = ops.project_adjoint(y2, g)
+    (a * xc).sum().backward()
+    assert torch.equal(y2.grad, ops.forward_project(xc, g))
+
+
+def test_layers_follow_listing1(ops):
+    """Listing 1 flow: ConeProjectionFor3D().forward(phantom[None], geom), then
+    ConeBackProjectionFor3D().forward(sinogram, geom), with a leading batch dimension."""
+    case = SMALL[2]
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    x = case.phantom()
+    sino = ops.ConeProjectionFor3D().forward(to_dev(x[None]), g)
+    assert tuple(sino.shape) == (1,) + og.sino_shape
+    reco = ops.ConeBackProjectionFor3D().forward(sino, g)
+    assert tuple(reco.shape) == (1,) + tuple(x.shape)
+    assert rel_l2(host(reco[0]), oracle.bp(og, host(sino[0]))) <= 1e-5
+
+
+# ------------------------------------------------------------------------------------------------
+# edge cases
+# ------------------------------------------------------------------------------------------------
+
+def test_rays_missing_the_volume_give_zero(ops):
+    from paper_2511_08427_gb300.operators import Geometry
+    g = Geometry.cone_circular((8, 8, 8), (1, 1, 1), (6, 6), (1, 1), 4, 2 * math.pi, 50.0, 80.0,
+                               detector_offset=(500.0, 0.0))
+    p = ops.forward_project(torch.ones((8, 8, 8), device=DEV), g)
+    assert torch.count_nonzero(p) == 0
+    assert torch.count_nonzero(ops.adjoint(torch.ones_like(p), g)) == 0
+
+
+def test_degenerate_single_voxel_single_pixel(ops):
+    from paper_2511_08427_gb300.operators import Geometry
+    g = Geometry.cone_circular((1, 1, 1), (1.0, 1.0, 1.0), (1, 1), (1.0, 1.0), 1, 2 * math.pi, 10.0, 20.0)
+    og = oracle.cone_circular((1, 1, 1), (1.0, 1.0, 1.0), (1, 1), (1.0, 1.0), 1, 2 * math.pi, 10.0, 20.0)
+    p = host(ops.forward_project(torch.full((1, 1, 1), 2.0, device=DEV), g))
+    # a unit-hat voxel on the central ray: dt * sum_k hat((k + 1/2) dt) = 1 for dt = 1/2 voxel
+    assert abs(p.item() - 2.0) < 1e-6
+    assert abs(p.item() - oracle.fp(og, np.full((1, 1, 1), 2.0)).item()) < 1e-6
+
+
+@pytest.mark.parametrize("dt", [0.2, 1.3])
+def test_custom_step(ops, dt):
+    case = SMALL[2]
+    g = case.library_geometry()
+    g.step = dt
+    og = case.oracle_geometry()
+    og.dt = dt
+    x = case.phantom()
+    for variant in (1, 2):
+        g.set_variant(0, variant)
+        assert rel_l2(host(ops.forward_project(to_dev(x), g)), oracle.fp(og, x)) <= 1e-5
+    y = inputs.gaussian(og.sino_shape, seed=2)
+    assert rel_l2(host(ops.adjoint(to_dev(y), g)), oracle.adjoint(og, y)) <= 1e-5
+
+
+def test_many_views_times_batch_splits_launches(ops):
+    from paper_2511_08427_gb300.operators import Geometry
+    V, B = 3000, 25            # V * B > 65535 grid rows: the launcher splits the batch
+    g = Geometry.parallel2d((6, 7), (1.0, 1.0), 5, 1.0, V)
+    x = torch.rand((B, 6, 7), device=DEV)
+    p = ops.forward_project(x, g)
+    for i in (0, 12, 24):
+        assert torch.equal(p[i], ops.forward_project(x[i].contiguous(), g))
+
+
+def test_misaligned_pointer_is_rejected(ops):
+    from paper_2511_08427_gb300 import PyronnError
+    case = SMALL[0]
+    g = case.library_geometry()
+    n = int(np.prod(case.params["vol_shape"]))
+    buf = torch.zeros(n + 1, device=DEV)
+    with pytest.raises(PyronnError) as e:
+        ops.forward_project(buf[1:].view(case.params["vol_shape"]), g)
+    assert e.value.code == -3
+
+
+def test_host_buffer_entry_point(ops):
+    import ctypes
+    from paper_2511_08427_gb300 import _lib
+    case = SMALL[2]
+    g = case.library_geometry()
+    x = case.phantom().astype(np.float32)
+    out = np.zeros(case.oracle_geometry().sino_shape, dtype=np.float32)
+    _lib.check(_lib.lib().pyronn_fp_host(g.handle, x.ctypes.data_as(ctypes.c_void_p),
+                                         out.ctypes.data_as(ctypes.c_void_p), 0, 1, None))
+    assert rel_l2(out, oracle_fp(case, x)) <= 1e-5
+
+
+# ------------------------------------------------------------------------------------------------
+# benchmark configurations at full size
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", [CFG1, CFG2], ids=lambda c: c.name)
+def test_2d_configs_full(ops, case):
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    x = cfg_phantom(case)
+    p = host(ops.forward_project(to_dev(x), g))
+    assert rel_l2(sino3(case, p), oracle.fp(og, x)) <= 1e-5
+    y = inputs.gaussian(og.sino_shape, seed=22)
+    a = host(ops.adjoint(to_dev(y.reshape(og.n_views, -1)), g))
+    assert rel_l2(a.reshape(og.vol_shape), oracle.adjoint(og, y)) <= 1e-5
+    b = host(ops.back_project(to_dev(y.reshape(og.n_views, -1)), g))
+    assert rel_l2(b.reshape(og.vol_shape), oracle.bp(og, y)) <= 1e-5
+
+
+def test_cone256_config_sampled(ops):
+    """256^3 cone beam, 360 views, 512^2 detector: sampled rays / voxels, sparse cotangent."""
+    case = CFG3
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    x = cfg_phantom(case)
+    xd = to_dev(x)
+    p = ops.forward_project(xd, g)
+    rng = np.random.default_rng(0)
+    n_rays = og.n_views * og.det_shape[0] * og.det_shape[1]
+    ids = rng.choice(n_rays, size=3000, replace=False)
+    ref = oracle.fp_rays(og, x, ids)
+    got = host(p).ravel()[ids]
+    assert rel_l2(got, ref) <= 1e-5
+    # matched adjoint of a sparse cotangent, compared over the whole volume
+    sid = rng.choice(n_rays, size=400, replace=False)
+    vals = rng.standard_normal(400)
+    y = torch.zeros(n_rays, device=DEV)
+    y[torch.from_numpy(sid).to(DEV)] = torch.from_numpy(vals.astype(np.float32)).to(DEV)
+    a = host(ops.adjoint(y.view(og.sino_shape), g))
+    refa = oracle.adjoint_rays(og, sid, vals.astype(np.float32).astype(np.float64))
+    assert rel_l2(a, refa) <= 1e-5
+    # voxel-driven BP of the projection, sampled voxels
+    b = host(ops.back_project(p, g, 1))
+    vids = rng.choice(x.size, size=3000, replace=False)
+    refb = oracle.bp_voxels(og, host(p), vids, 1)
+    assert rel_l2(b.ravel()[vids], refb) <= 1e-5
+    # dot-product test at full size
+    yc = torch.randn(og.sino_shape, device=DEV)
+    lhs = float(np.vdot(host(p).ravel(), host(yc).ravel()))
+    rhs = float(np.vdot(x.astype(np.float64).ravel(), host(ops.adjoint(yc, g)).ravel()))
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+def test_variants_agree_at_full_size(ops):
+    case = CFG3
+    g = case.library_geometry()
+    x = to_dev(cfg_phantom(case))
+    g.set_variant(0, 1)
+    p1 = ops.forward_project(x, g)
+    g.set_variant(0, 2)
+    p2 = ops.forward_project(x, g)
+    assert rel_l2(host(p2), host(p1)) <= 2e-6
+    assert g.read_flags()[:3] == [0, 0, 0]
