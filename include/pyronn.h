@@ -180,10 +180,13 @@ PYRONN_API int pyronn_fp_host(pyronn_geom_t g, const void *vol_host, void *sino_
 PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void *vol_host, int dtype, int batch,
                         void *stream);
 
-/* Kernel variant of an operator, for tests and tuning: op 0 = forward projection
- * (variant 0 automatic, 1 one-thread-per-ray read-only-cache kernel, 2 slab-staged shared-memory
- * kernel; 2 falls back to 1 when the staged box cannot fit in shared memory). All variants
- * compute the same operator. */
+/* Kernel variant of an operator, for tests and tuning. op 0 = forward projection: variant 0
+ * automatic (= 3 where usable, else 2), 1 one-thread-per-ray read-only-cache kernel, 2 slab-staged
+ * shared-memory kernel filled by thread loads (falls back to 1 when the staged box cannot fit),
+ * 3 slab-staged kernel filled by TMA tensor copies (needs a row pitch that is a multiple of 16
+ * bytes; falls back to 2). op 1 = matched adjoint:
+ * variant 0 automatic (= 2), 1 one-thread-per-ray FP32 global atomics, 2 output-stationary
+ * bricks accumulated in shared memory. All variants compute the same operator. */
 PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
 
 /* ------------------------------------------------------------------------------------------
@@ -193,8 +196,17 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
 /* Read (and optionally reset) the geometry's device diagnostic counters, 8 ints: [0] samples of
  * the slab-staged projector that fell outside their staged box and were read from global memory
  * instead, [1] rays sampled outside the slab march (nearly parallel to the slabs), [2] slabs whose
- * box exceeded shared memory. Synchronous (device-wide copy). All zero is the expected state. */
+ * box exceeded shared memory, [3] tensor copies that did not complete within the bounded wait (the
+ * launch then stops early and its output is invalid). Synchronous (device-wide copy). All zero is
+ * the expected state. */
 PYRONN_API int pyronn_geom_read_flags(pyronn_geom_t g, int *out, int reset);
+
+/* Forward-projector configuration that would be used for element type dtype (host computation,
+ * no GPU needed), 16 ints: [0] kernel (1 direct, 2 slab thread-staged, 3 slab TMA-staged),
+ * [1] slab depth, [2] guard planes, [3] first slab plane, [4..12] TMA box (x, y, z) for march
+ * axes x, y, z, [13] elements per TMA buffer, [14] dynamic shared memory bytes per CTA,
+ * [15] thread-staged box capacity (elements). */
+PYRONN_API int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out);
 
 /* Message describing the last error of the calling thread ("" if none). */
 PYRONN_API const char *pyronn_last_error(void);

@@ -184,6 +184,7 @@ int finalize_geometry(pyronn_geom *g) {
     const int V = g->n_views;
     g->fp_rec.assign(V, FpRec{});
     g->bp_rec.assign(V, BpRec{});
+    g->views_ext.assign((size_t)V * VIEW64_STRIDE, 0.0);
     const double C[3] = {g->ox, g->oy, g->oz};
     const double s[3] = {g->sx, g->sy, g->sz};
     const double hu = 0.5 * (g->nu - 1), hv = 0.5 * (g->nv - 1);
@@ -212,6 +213,16 @@ int finalize_geometry(pyronn_geom *g) {
                 Rv[i] = lam * col1[i];
                 B0[i] = col2[i]; Bu[i] = col0[i]; Bv[i] = col1[i];
             }
+            double *x = &g->views_ext[(size_t)n * VIEW64_STRIDE];
+            for (int row = 0; row < 3; ++row) {
+                for (int a = 0; a < 3; ++a) x[4 * row + a] = r[4 * row + a];
+                x[4 * row + 3] = r[4 * row + 0] * C[0] + r[4 * row + 1] * C[1] + r[4 * row + 2] * C[2] + r[4 * row + 3];
+            }
+            for (int i = 0; i < 3; ++i) {
+                x[12 + i] = S[i] - C[i];
+                x[15 + i] = col0[i]; x[18 + i] = col1[i]; x[21 + i] = col2[i]; x[24 + i] = nrm[i];
+            }
+            x[27] = den;
             // BP: centred voxel index -> centred detector coordinate times w
             for (int row = 0; row < 3; ++row) {
                 for (int a = 0; a < 3; ++a) Pc[4 * row + a] = r[4 * row + a] * s[a];
@@ -228,6 +239,10 @@ int finalize_geometry(pyronn_geom *g) {
                 Ru[i] = g->du * eu[i];
                 Rv[i] = g->dv * ev[i];
                 B0[i] = d[i]; Bu[i] = 0.0; Bv[i] = 0.0;
+            }
+            double *x = &g->views_ext[(size_t)n * VIEW64_STRIDE];
+            for (int i = 0; i < 3; ++i) {
+                x[i] = Dc[i] - C[i]; x[3 + i] = eu[i]; x[6 + i] = ev[i]; x[9 + i] = d[i];
             }
             double CD[3] = {C[0] - Dc[0], C[1] - Dc[1], C[2] - Dc[2]};
             for (int a = 0; a < 3; ++a) {
@@ -248,6 +263,7 @@ int finalize_geometry(pyronn_geom *g) {
     }
     g->sample_count = -1;
     g->fp_cfg_ready = 0;
+    g->tma_ready[0] = g->tma_ready[1] = g->tma_ready[2] = 0;
     return PYRONN_OK;
 }
 
@@ -287,6 +303,18 @@ int ensure_device(pyronn_geom *g) {
         cudaFree(pb);
         return set_error(PYRONN_CUDA_ERROR, "upload of view tables: %s", cudaGetErrorString(e));
     }
+    void *pv = nullptr;
+    e = cudaMalloc(&pv, sizeof(double) * g->views_ext.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pv, g->views_ext.data(), sizeof(double) * g->views_ext.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(pv);
+        cudaFree(pg);
+        cudaFree(pf);
+        cudaFree(pb);
+        return set_error(PYRONN_CUDA_ERROR, "upload of FP64 views: %s", cudaGetErrorString(e));
+    }
+    g->d_views64 = (double *)pv;
     g->d_flags = (int *)pg;
     g->d_fp = (FpRec *)pf;
     g->d_bp = (BpRec *)pb;
@@ -309,6 +337,9 @@ OpParams make_params(const pyronn_geom *g, int batch) {
     p.fp = g->d_fp;
     p.bp = g->d_bp;
     p.flags = g->d_flags;
+    p.views64 = g->d_views64;
+    p.sx = g->sx; p.sy = g->sy; p.sz = g->sz;
+    p.du = g->du; p.dv = g->dv; p.ou = g->ou; p.ov = g->ov;
     p.vol_elems = (long long)g->nx * g->ny * g->nz;
     p.sino_elems = (long long)g->nu * g->nv * g->n_views;
     return p;
@@ -478,6 +509,7 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
         cudaFree(g->d_fp);
         cudaFree(g->d_bp);
         cudaFree(g->d_flags);
+        cudaFree(g->d_views64);
         cudaFree(g->d_scratch);
         cudaFree(g->d_stage_in);
         cudaFree(g->d_stage_out);
@@ -494,6 +526,7 @@ int pyronn_geom_set_step(pyronn_geom_t g, double dt_mm) {
     g->dt = dt_mm;
     g->sample_count = -1;
     g->fp_cfg_ready = 0;
+    g->tma_ready[0] = g->tma_ready[1] = g->tma_ready[2] = 0;
     return PYRONN_OK;
 }
 

@@ -1,0 +1,489 @@
+// TMA-staged ray-driven forward projector (same operator as fp_direct_kernel, Sec. 2.1).
+//
+// Structure as in k_fp_slab.cu (one CTA per 16 x 16 detector tile of one view, slabs of D
+// planes along the tile's dominant axis m, exact sample partition through integer slab
+// boundaries), but the slab box is moved by the Tensor Memory Accelerator: one thread issues a
+// cp.async.bulk.tensor load of a fixed-size box (chosen on the host as the largest footprint of
+// any tile), the hardware zero-fills everything outside the volume, and two buffers let the load
+// of slab s + 1 run under the sampling of slab s. Completion is tracked by mbarrier transaction
+// counts; every wait is bounded, and a CTA whose copy does not arrive sets an error counter and
+// leaves.
+//
+// Sample loop: positions relative to the box origin, floor / fraction by the round-down
+// magic-number addition (no conversion-pipe instructions), eight shared-memory reads, seven
+// lerps, one accumulate.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <thread>
+#include <type_traits>
+
+#include "device_common.cuh"
+
+namespace pyronn {
+
+constexpr int TMA_TU = 16, TMA_TV = 16, TMA_NT = TMA_TU * TMA_TV;
+constexpr unsigned TMA_WAIT_LIMIT = 1u << 20;   // try_wait polls before a copy counts as lost
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    for (unsigned i = 0; i < TMA_WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *map, unsigned bar, int x, int y, int z,
+                                            int b) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(b), "r"(bar)
+        : "memory");
+}
+
+// floor and fraction of q in [-2^22, 2^22): q + 1.5 * 2^23 rounded down is an integer
+__device__ __forceinline__ void floor_frac(float q, int &i, float &f) {
+    const float M = 12582912.0f;
+    float t = __fadd_rd(q, M);
+    i = __float_as_int(t) - 0x4B400000;
+    f = q - (t - M);
+}
+
+struct TmaMaps {
+    CUtensorMap map[3];   // one box shape per march axis
+};
+
+struct SlabBox {
+    int lo[3];      // box origin (x aligned for TMA)
+    bool fits;      // the tile's footprint in this slab fits the box
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox cfg,
+                                                           const __grid_constant__ TmaMaps maps,
+                                                           const T *__restrict__ vol, T *__restrict__ sino) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations: 128-byte aligned by construction (the launch adds 128 bytes of slack)
+    const unsigned raw_u32 = smem_u32(smem_raw);
+    const unsigned pad = ((raw_u32 + 127u) & ~127u) - raw_u32;
+    T *const buf0 = (T *)(smem_raw + pad);
+    T *const buf1 = (T *)(smem_raw + pad + sizeof(T) * (size_t)cfg.buf_elems);
+    __shared__ __align__(8) unsigned long long s_bar[2];
+    __shared__ float s_corner[5][6];
+    __shared__ int s_srange[2];
+
+    const int view = blockIdx.z % p.n_views;
+    const int b = blockIdx.z / p.n_views;
+    const int tu0 = blockIdx.x * TMA_TU, tv0 = blockIdx.y * TMA_TV;
+    const int tu1 = min(tu0 + TMA_TU, p.det.nu) - 1, tv1 = min(tv0 + TMA_TV, p.det.nv) - 1;
+    const int tid = threadIdx.x;
+    const int u = tu0 + tid % TMA_TU, v = tv0 + tid / TMA_TU;
+    const bool active = (u <= tu1) && (v <= tv1);
+    const FpRec &rec = p.fp[view];
+    const T *vb = vol + (long long)b * p.vol_elems;
+
+    if (tid < 5) {
+        float cu, cv;
+        if (tid < 4) {
+            cu = (float)((tid & 1) ? tu1 : tu0);
+            cv = (float)((tid & 2) ? tv1 : tv0);
+        } else {
+            cu = 0.5f * (float)(tu0 + tu1);
+            cv = 0.5f * (float)(tv0 + tv1);
+        }
+        RayIdx c = ray_setup(rec, p.vol, cu, cv);
+        s_corner[tid][0] = c.cx; s_corner[tid][1] = c.cy; s_corner[tid][2] = c.cz;
+        s_corner[tid][3] = c.dx; s_corner[tid][4] = c.dy; s_corner[tid][5] = c.dz;
+    }
+    if (tid == 0) {
+        s_srange[0] = 1 << 30;
+        s_srange[1] = -(1 << 30);
+        mbar_init(smem_u32(&s_bar[0]), 1);
+        mbar_init(smem_u32(&s_bar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    RayIdx r = ray_setup(rec, p.vol, (float)min(u, tu1), (float)min(v, tv1));
+    int k0 = 0, k1 = -1;
+    bool hit = active && ray_k_range(r, p.vol, p.dt, k0, k1);
+    __syncthreads();
+
+    int m;
+    {
+        float ax = fabsf(s_corner[4][3]), ay = fabsf(s_corner[4][4]), az = fabsf(s_corner[4][5]);
+        m = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    }
+    const int a1 = (m == 0) ? 1 : 0, a2 = (m == 2) ? 1 : 2;
+    const int dims[3] = {p.vol.nx, p.vol.ny, p.vol.nz};
+    const int Nm = dims[m];
+    const float cm = m == 0 ? r.cx : (m == 1 ? r.cy : r.cz);
+    const float dm = m == 0 ? r.dx : (m == 1 ? r.dy : r.dz);
+    const bool marchable = fabsf(dm) > 1e-3f * (fabsf(r.dx) + fabsf(r.dy) + fabsf(r.dz));
+    const bool direct_ray = hit && !marchable;
+    if (direct_ray) hit = false;
+    const bool pos = dm > 0.0f;
+    const float inv_step = marchable ? 1.0f / (p.dt * dm) : 0.0f;
+    const int D = cfg.depth, G = cfg.guard;
+    const int base0 = cfg.slab0;                        // slab s covers floor(q_m) in [base0 + s D, base0 + (s+1) D)
+    const int nslab_all = (Nm + 1 - base0 + D - 1) / D; // enough slabs to reach plane Nm - 1
+    const int BXb = cfg.bx[m], BYb = cfg.by[m], BZb = cfg.bz[m];
+    const int box_elems = BXb * BYb * BZb;
+    const unsigned box_bytes = (unsigned)(sizeof(T) * box_elems);
+    const CUtensorMap *tmap = &maps.map[m];
+
+    // slab range of this tile: union of the rays' in-box sample ranges
+    if (hit) {
+        float qa = fmaf(fmaf((float)k0, p.dt, 0.5f * p.dt), dm, cm);
+        float qb = fmaf(fmaf((float)k1, p.dt, 0.5f * p.dt), dm, cm);
+        float qlo = fmaxf(fminf(qa, qb), -1.0f), qhi = fminf(fmaxf(qa, qb), (float)Nm);
+        int slo = ((int)floorf(qlo) - base0) / D, shi = ((int)floorf(qhi) - base0) / D;
+        slo = max(min(slo, nslab_all - 1), 0);
+        shi = max(min(shi, nslab_all - 1), 0);
+        atomicMin(&s_srange[0], slo);
+        atomicMax(&s_srange[1], shi);
+    }
+    __syncthreads();
+    const int s_first = s_srange[0], s_last = s_srange[1];
+    const int nsl = s_last >= s_first ? s_last - s_first + 1 : 0;
+    const unsigned bars[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const int align = 16 / (int)sizeof(T);
+
+    // box of slab s (uniform across the CTA)
+    auto slab_box = [&](int s) {
+        SlabBox sb;
+        const int b_lo = base0 + s * D;
+        const int b_hi = min(b_lo + D, Nm);
+        int lo[3], hi[3];
+        lo[m] = b_lo - G;
+        hi[m] = b_hi + G;
+        float mn1 = 3e38f, mx1 = -3e38f, mn2 = 3e38f, mx2 = -3e38f;
+        const float planes[2] = {(float)(b_lo - G), (float)(b_hi + G)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float *cr = s_corner[c];
+            float idm = 1.0f / cr[3 + m];
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+                float t = (planes[pl] - cr[m]) * idm;
+                float q1 = fmaf(t, cr[3 + a1], cr[a1]);
+                float q2 = fmaf(t, cr[3 + a2], cr[a2]);
+                mn1 = fminf(mn1, q1); mx1 = fmaxf(mx1, q1);
+                mn2 = fminf(mn2, q2); mx2 = fmaxf(mx2, q2);
+            }
+        }
+        const float gf = (float)(G + 2);
+        mn1 = fmaxf(mn1, -gf); mx1 = fminf(mx1, (float)dims[a1] + gf);
+        mn2 = fmaxf(mn2, -gf); mx2 = fminf(mx2, (float)dims[a2] + gf);
+        lo[a1] = max((int)floorf(mn1) - 1, -1 - G);
+        hi[a1] = min((int)floorf(mx1) + 2, dims[a1] + G);
+        lo[a2] = max((int)floorf(mn2) - 1, -1 - G);
+        hi[a2] = min((int)floorf(mx2) + 2, dims[a2] + G);
+        // TMA: the innermost start coordinate must be 16-byte aligned
+        int x0 = lo[0] >= 0 ? (lo[0] / align) * align : -(((-lo[0]) + align - 1) / align) * align;
+        sb.lo[0] = x0; sb.lo[1] = lo[1]; sb.lo[2] = lo[2];
+        sb.fits = (hi[0] - x0 + 1 <= BXb) && (hi[1] - lo[1] + 1 <= BYb) && (hi[2] - lo[2] + 1 <= BZb);
+        return sb;
+    };
+
+    float acc = 0.0f;
+    const float hdt = 0.5f * p.dt;
+    if (nsl > 0) {
+        if (tid == 0) {
+            SlabBox sb0 = slab_box(s_first);
+            mbar_expect_tx(bars[0], box_bytes);
+            tma_load_4d(smem_u32(buf0), tmap, bars[0], sb0.lo[0], sb0.lo[1], sb0.lo[2], b);
+        }
+        for (int i = 0; i < nsl; ++i) {
+            const int s = s_first + i;
+            const int bi = i & 1;
+            if (tid == 0 && i + 1 < nsl) {
+                SlabBox sbn = slab_box(s + 1);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(bars[bi ^ 1], box_bytes);
+                tma_load_4d(smem_u32(bi ? buf0 : buf1), tmap, bars[bi ^ 1], sbn.lo[0], sbn.lo[1], sbn.lo[2], b);
+            }
+            const SlabBox sb = slab_box(s);
+            bool ok = mbar_wait_bounded(bars[bi], (unsigned)((i >> 1) & 1));
+            // a copy lost anywhere aborts every CTA at its next slab, so the launch ends promptly
+            if (tid == 0 && *(volatile int *)(p.flags + FLAG_TMA_TIMEOUT) != 0) ok = false;
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) atomicAdd(p.flags + FLAG_TMA_TIMEOUT, 1);
+                // wait (bounded) for the copies still in flight before the shared memory goes away
+                mbar_wait_bounded(bars[bi], (unsigned)((i >> 1) & 1));
+                if (i + 1 < nsl) mbar_wait_bounded(bars[bi ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+                return;
+            }
+            const int b_lo = base0 + s * D;
+            const int b_hi = min(b_lo + D, Nm);
+            int ka = 0, kb = -1;
+            if (hit) {
+                if (pos) {
+                    ka = (int)ceilf(fmaf((float)b_lo - cm, inv_step, -0.5f));
+                    kb = (int)ceilf(fmaf((float)b_hi - cm, inv_step, -0.5f)) - 1;
+                } else {
+                    ka = (int)floorf(fmaf((float)b_hi - cm, inv_step, -0.5f)) + 1;
+                    kb = (int)floorf(fmaf((float)b_lo - cm, inv_step, -0.5f));
+                }
+                ka = max(ka, k0);
+                kb = min(kb, k1);
+            }
+            if (sb.fits) {
+                const T *box = bi ? buf1 : buf0;
+                const int sy = BXb, sz = BXb * BYb;
+                const int limit = box_elems - (sz + sy + 1);
+                // position relative to the box origin: q = c0 + kf * step
+                const float c0x = fmaf(hdt, r.dx, r.cx - (float)sb.lo[0]);
+                const float c0y = fmaf(hdt, r.dy, r.cy - (float)sb.lo[1]);
+                const float c0z = fmaf(hdt, r.dz, r.cz - (float)sb.lo[2]);
+                const float stx = p.dt * r.dx, sty = p.dt * r.dy, stz = p.dt * r.dz;
+                float kf = (float)ka;
+                for (int k = ka; k <= kb; ++k, kf += 1.0f) {
+                    const float qx = fmaf(kf, stx, c0x), qy = fmaf(kf, sty, c0y), qz = fmaf(kf, stz, c0z);
+                    int ix, iy, iz;
+                    float ax, ay, az;
+                    floor_frac(qx, ix, ax);
+                    floor_frac(qy, iy, ay);
+                    floor_frac(qz, iz, az);
+                    const int base = iz * sz + iy * sy + ix;
+                    if ((unsigned)base > (unsigned)limit) {
+                        atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
+                        acc += trilerp_zero(vb, p.vol, qx + (float)sb.lo[0], qy + (float)sb.lo[1],
+                                            qz + (float)sb.lo[2]);
+                        continue;
+                    }
+                    const T *s0 = box + base;
+                    const float v000 = to_f32(s0[0]), v001 = to_f32(s0[1]);
+                    const float v010 = to_f32(s0[sy]), v011 = to_f32(s0[sy + 1]);
+                    const float v100 = to_f32(s0[sz]), v101 = to_f32(s0[sz + 1]);
+                    const float v110 = to_f32(s0[sz + sy]), v111 = to_f32(s0[sz + sy + 1]);
+                    const float c00 = fmaf(ax, v001 - v000, v000);
+                    const float c01 = fmaf(ax, v011 - v010, v010);
+                    const float c10 = fmaf(ax, v101 - v100, v100);
+                    const float c11 = fmaf(ax, v111 - v110, v110);
+                    const float c0 = fmaf(ay, c01 - c00, c00);
+                    const float c1 = fmaf(ay, c11 - c10, c10);
+                    acc += fmaf(az, c1 - c0, c0);
+                }
+            } else {
+                if (tid == 0) atomicAdd(p.flags + FLAG_SLAB_OVERFLOW, 1);
+                for (int k = ka; k <= kb; ++k) {
+                    float t = fmaf((float)k, p.dt, hdt);
+                    acc += trilerp_zero(vb, p.vol, fmaf(t, r.dx, r.cx), fmaf(t, r.dy, r.cy), fmaf(t, r.dz, r.cz));
+                }
+            }
+            __syncthreads();   // everyone is done with buf[bi] before it is refilled
+        }
+    }
+    if (direct_ray) {
+        atomicAdd(p.flags + FLAG_SLAB_DIRECT_RAY, 1);
+        for (int k = k0; k <= k1; ++k) {
+            float t = fmaf((float)k, p.dt, hdt);
+            acc += trilerp_zero(vb, p.vol, fmaf(t, r.dx, r.cx), fmaf(t, r.dy, r.cy), fmaf(t, r.dz, r.cz));
+        }
+    }
+    if (active)
+        sino[(long long)b * p.sino_elems + ((long long)view * p.det.nv + v) * p.det.nu + u] = from_f32<T>(acc * p.dt);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host: box bound per march axis, tensor map, launch
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+struct RayD {
+    double c[3], d[3];
+};
+
+RayD ray_setup_d(const FpRec &r, const pyronn_geom *g, double u, double v) {
+    double Y[3], D[3];
+    for (int i = 0; i < 3; ++i) {
+        Y[i] = (double)r.R0[i] + u * r.Ru[i] + v * r.Rv[i];
+        D[i] = (double)r.B0[i] + u * r.Bu[i] + v * r.Bv[i];
+    }
+    double inv = 1.0 / std::sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    for (int i = 0; i < 3; ++i) D[i] *= inv;
+    double tau = -(Y[0] * D[0] + Y[1] * D[1] + Y[2] * D[2]);
+    const double is[3] = {1.0 / g->sx, 1.0 / g->sy, 1.0 / g->sz};
+    const double h[3] = {0.5 * (g->nx - 1), 0.5 * (g->ny - 1), 0.5 * (g->nz - 1)};
+    RayD o;
+    for (int i = 0; i < 3; ++i) {
+        o.c[i] = (Y[i] + tau * D[i]) * is[i] + h[i];
+        o.d[i] = D[i] * is[i];
+    }
+    return o;
+}
+
+// Per march axis, the largest cross-axis extents (in voxels) of any tile's staged box.
+void tile_extents(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0, int D, int G, int base0,
+                  double ext[3][3]) {
+    int tu1 = std::min(tu0 + TMA_TU, g->nu) - 1, tv1 = std::min(tv0 + TMA_TV, g->nv) - 1;
+    RayD cr[4];
+    for (int c = 0; c < 4; ++c) cr[c] = ray_setup_d(rec, g, (c & 1) ? tu1 : tu0, (c & 2) ? tv1 : tv0);
+    RayD ctr = ray_setup_d(rec, g, 0.5 * (tu0 + tu1), 0.5 * (tv0 + tv1));
+    const int dims[3] = {g->nx, g->ny, g->nz};
+    double amax = std::max(std::fabs(ctr.d[0]), std::max(std::fabs(ctr.d[1]), std::fabs(ctr.d[2])));
+    for (int m = 0; m < 3; ++m) {
+        if (std::fabs(ctr.d[m]) < 0.999 * amax) continue;
+        int a1 = (m == 0) ? 1 : 0, a2 = (m == 2) ? 1 : 2;
+        int Nm = dims[m];
+        int nslab = (Nm + 1 - base0 + D - 1) / D;
+        for (int which = 0; which < 2; ++which) {
+            int s = which ? nslab - 1 : 0;
+            int b_lo = base0 + s * D, b_hi = std::min(b_lo + D, Nm);
+            double planes[2] = {(double)(b_lo - G), (double)(b_hi + G)};
+            double mn1 = 1e300, mx1 = -1e300, mn2 = 1e300, mx2 = -1e300;
+            for (int c = 0; c < 4; ++c)
+                for (int pl = 0; pl < 2; ++pl) {
+                    double t = (planes[pl] - cr[c].c[m]) / cr[c].d[m];
+                    double q1 = cr[c].c[a1] + t * cr[c].d[a1], q2 = cr[c].c[a2] + t * cr[c].d[a2];
+                    mn1 = std::min(mn1, q1); mx1 = std::max(mx1, q1);
+                    mn2 = std::min(mn2, q2); mx2 = std::max(mx2, q2);
+                }
+            // kernel: lo = floor(mn) - 1, hi = floor(mx) + 2 (clipped); extent <= ceil(mx - mn) + 4, +2 for FP32
+            double e1 = std::min(std::ceil(mx1 - mn1) + 6.0, (double)(dims[a1] + 2 * G + 2));
+            double e2 = std::min(std::ceil(mx2 - mn2) + 6.0, (double)(dims[a2] + 2 * G + 2));
+            ext[m][a1] = std::max(ext[m][a1], e1);
+            ext[m][a2] = std::max(ext[m][a2], e2);
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+}  // namespace
+
+// Box dimensions for the TMA kernel, or depth = 0 if it cannot be used (shared memory too small or
+// the row pitch is not a multiple of 16 bytes).
+FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem) {
+    FpTmaBox c{};
+    const int align = 16 / (int)elem;
+    if (((size_t)g->nx * elem) % 16 != 0) return c;
+    c.depth = 8;
+    double smin = std::min(g->sx, std::min(g->sy, g->sz));
+    c.guard = 1 + (int)std::floor(g->dt / smin);
+    // slab planes start so that (first plane - guard) is a multiple of the x alignment
+    c.slab0 = -1 - (((-1 - c.guard) % align) + align) % align;
+    while (c.slab0 - c.guard > -1 - c.guard) c.slab0 -= align;   // keep the first slab at or below plane -1
+    const int ntu = (g->nu + TMA_TU - 1) / TMA_TU, ntv = (g->nv + TMA_TV - 1) / TMA_TV;
+    double ext[3][3] = {{0}};
+    std::atomic<int> next(0);
+    std::mutex mu;
+    auto work = [&]() {
+        double loc[3][3] = {{0}};
+        for (int n = next.fetch_add(1); n < g->n_views; n = next.fetch_add(1))
+            for (int j = 0; j < ntv; ++j)
+                for (int i = 0; i < ntu; ++i)
+                    tile_extents(g, g->fp_rec[n], i * TMA_TU, j * TMA_TV, c.depth, c.guard, c.slab0, loc);
+        std::lock_guard<std::mutex> lk(mu);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) ext[a][b] = std::max(ext[a][b], loc[a][b]);
+    };
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned i = 1; i < nt; ++i) th.emplace_back(work);
+    work();
+    for (auto &t : th) t.join();
+    const int dims[3] = {g->nx, g->ny, g->nz};
+    int maxel = 0;
+    for (int m = 0; m < 3; ++m) {
+        int e[3];
+        for (int a = 0; a < 3; ++a) {
+            if (a == m) e[a] = std::min(c.depth + 2 * c.guard + 1, dims[a] + 2 * c.guard + 2);
+            else e[a] = (int)ext[m][a];
+            if (a != m && e[a] == 0) e[a] = 1;   // axis never chosen: keep a valid box
+        }
+        // x is the innermost TMA dimension: round up, plus room for the aligned start unless the slab
+        // planes themselves start aligned (march along x)
+        e[0] = m == 0 ? ((e[0] + align - 1) / align) * align : ((e[0] + 2 * (align - 1)) / align) * align;
+        for (int a = 0; a < 3; ++a) e[a] = std::min(e[a], 256);
+        c.bx[m] = e[0]; c.by[m] = e[1]; c.bz[m] = e[2];
+        maxel = std::max(maxel, e[0] * e[1] * e[2]);
+    }
+    c.buf_elems = ((maxel * (int)elem + 127) / 128) * 128 / (int)elem;
+    if (2 * (size_t)c.buf_elems * elem > 200 * 1024) c.depth = 0;   // does not fit: use another kernel
+    return c;
+}
+
+template <typename T>
+static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, cudaStream_t st) {
+    auto enc = encode_fn();
+    if (!enc) return (int)cudaErrorNotSupported;
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    const size_t smem = 2 * sizeof(T) * (size_t)cfg.buf_elems + 128;
+    cudaError_t e = cudaFuncSetAttribute(fp_tma_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    const int nx = p.vol.nx, ny = p.vol.ny, nz = p.vol.nz;
+    const int per_launch = 65535 / p.n_views > 0 ? 65535 / p.n_views : 1;
+    for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
+        const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
+        const T *vptr = (const T *)vol + b0 * p.vol_elems;
+        TmaMaps maps;
+        std::memset(&maps, 0, sizeof(maps));
+        cuuint64_t gdim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nb};
+        cuuint64_t gstride[3] = {(cuuint64_t)nx * sizeof(T), (cuuint64_t)nx * ny * sizeof(T),
+                                 (cuuint64_t)nx * ny * nz * sizeof(T)};
+        cuuint32_t estride[4] = {1, 1, 1, 1};
+        for (int m = 0; m < 3; ++m) {
+            cuuint32_t box[4] = {(cuuint32_t)cfg.bx[m], (cuuint32_t)cfg.by[m], (cuuint32_t)cfg.bz[m], 1};
+            CUresult r = enc(&maps.map[m], dt, 4, (void *)vptr, gdim, gstride, box, estride,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
+        }
+        dim3 grid(ceil_div(p.det.nu, TMA_TU), ceil_div(p.det.nv, TMA_TV), p.n_views * nb);
+        fp_tma_kernel<T><<<grid, TMA_NT, smem, st>>>(p, cfg, maps, vptr, (T *)sino + b0 * p.sino_elems);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_tma_t<float>(p, cfg, vol, sino, st);
+        case PYRONN_BF16: return launch_tma_t<__nv_bfloat16>(p, cfg, vol, sino, st);
+        case PYRONN_F16: return launch_tma_t<__half>(p, cfg, vol, sino, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pyronn

@@ -76,6 +76,15 @@ const FpSlabCfg &fp_cfg(pyronn_geom_t g) {
     return g->fp_cfg;
 }
 
+const FpTmaBox &tma_cfg(pyronn_geom_t g, int dtype) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (!g->tma_ready[dtype]) {
+        g->tma_cfg[dtype] = choose_fp_tma_box(g, dtype_size(dtype));
+        g->tma_ready[dtype] = 1;
+    }
+    return g->tma_cfg[dtype];
+}
+
 }  // namespace
 
 extern "C" {
@@ -88,15 +97,47 @@ int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch
     OpParams p = make_params(g, batch);
     if (g->fp_variant == 1)
         return cuda_rc(launch_fp_direct(p, vol, sino, dtype, stream), "forward projection launch");
+    if (g->fp_variant == 0 || g->fp_variant == 3) {
+        const FpTmaBox &tb = tma_cfg(g, dtype);
+        if (tb.depth > 0) return cuda_rc(launch_fp_tma(p, tb, vol, sino, dtype, stream), "forward projection launch");
+    }
     return cuda_rc(launch_fp(p, fp_cfg(g), vol, sino, dtype, stream), "forward projection launch");
+}
+
+int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out) {
+    clear_error();
+    if (!g || !out) return set_error(PYRONN_INVALID_ARG, "null argument");
+    if (dtype_size(dtype) == 0) return set_error(PYRONN_UNSUPPORTED_DTYPE, "unsupported dtype %d", dtype);
+    for (int i = 0; i < 16; ++i) out[i] = 0;
+    const FpTmaBox &tb = tma_cfg(g, dtype);
+    const FpSlabCfg &sc = fp_cfg(g);
+    int kernel = 1;
+    if (g->fp_variant == 1) kernel = 1;
+    else if ((g->fp_variant == 0 || g->fp_variant == 3) && tb.depth > 0) kernel = 3;
+    else if (sc.valid) kernel = 2;
+    out[0] = kernel;
+    out[1] = kernel == 3 ? tb.depth : sc.depth;
+    out[2] = kernel == 3 ? tb.guard : sc.guard;
+    out[3] = tb.slab0;
+    for (int m = 0; m < 3; ++m) {
+        out[4 + 3 * m] = tb.bx[m];
+        out[5 + 3 * m] = tb.by[m];
+        out[6 + 3 * m] = tb.bz[m];
+    }
+    out[13] = tb.buf_elems;
+    out[14] = kernel == 3 ? (int)(2 * dtype_size(dtype) * (size_t)tb.buf_elems + 128)
+                          : (kernel == 2 ? (int)(sizeof(float) * (size_t)sc.smem_floats) : 0);
+    out[15] = sc.smem_floats;
+    return PYRONN_OK;
 }
 
 int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
-    if (op != 0) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
-    if (variant < 0 || variant > 2) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
-    g->fp_variant = variant;
+    if (op != 0 && op != 1) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
+    if (variant < 0 || variant > (op == 0 ? 3 : 2)) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
+    if (op == 0) g->fp_variant = variant;
+    else g->adj_variant = variant;
     return PYRONN_OK;
 }
 
@@ -106,6 +147,7 @@ int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int dtype, int 
     if (rc) return rc;
     if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
     OpParams p = make_params(g, batch);
+    if (g->adj_variant != 1) return cuda_rc(launch_adjoint_brick(p, sino, vol, dtype, stream), "adjoint launch");
     float *acc = nullptr;
     if (dtype != PYRONN_F32) {
         if ((rc = ensure_scratch(g, sizeof(float) * (size_t)p.vol_elems * batch))) return rc;

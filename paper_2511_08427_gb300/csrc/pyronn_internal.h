@@ -55,10 +55,21 @@ struct OpParams {
     long long vol_elems;   // elements per volume
     long long sino_elems;  // elements per sinogram
     int *flags;            // device diagnostic counters (geometry-owned, see pyronn_geom_read_flags)
+    // FP64 description (for per-brick constants computed on the device in double precision)
+    const double *views64; // device, n_views x VIEW64_STRIDE extended FP64 records (see geometry.cpp)
+    double sx, sy, sz;     // voxel spacing, mm
+    double du, dv, ou, ov; // detector spacing / offset, mm
 };
 
+// Extended FP64 per-view record (all positions relative to the volume centre C, world mm):
+//   perspective: [0..11] P with C folded in (maps X - C to (u w, v w, w)), [12..14] S - C,
+//                [15..17] du eu, [18..20] dv ev, [21..23] D0 - S, [24..26] (du eu) x (dv ev),
+//                [27] (D0 - S) . normal
+//   parallel:    [0..2] Dc - C, [3..5] eu, [6..8] ev, [9..11] d (unit ray direction)
+constexpr int VIEW64_STRIDE = 32;
+
 // Diagnostic counters (device, per geometry).
-enum { FLAG_SLAB_OUT_OF_BOX = 0, FLAG_SLAB_DIRECT_RAY = 1, FLAG_SLAB_OVERFLOW = 2, N_FLAGS = 8 };
+enum { FLAG_SLAB_OUT_OF_BOX = 0, FLAG_SLAB_DIRECT_RAY = 1, FLAG_SLAB_OVERFLOW = 2, FLAG_TMA_TIMEOUT = 3, N_FLAGS = 8 };
 
 // Launch configuration of the slab-staged forward projector (chosen per geometry).
 struct FpSlabCfg {
@@ -67,6 +78,13 @@ struct FpSlabCfg {
     int guard;             // extra staged planes on each side of a slab
     int smem_floats;       // staged box capacity
     int valid;             // 0: use the direct kernel
+};
+
+// Box shapes of the TMA-staged forward projector (chosen per geometry and element size).
+struct FpTmaBox {
+    int bx[3], by[3], bz[3];   // box extents (x, y, z) for march axis m = 0, 1, 2
+    int depth, guard, slab0;   // slab depth (0: kernel unusable), guard planes, first slab plane
+    int buf_elems;             // elements per buffer (max over axes)
 };
 
 }  // namespace pyronn
@@ -87,6 +105,7 @@ struct pyronn_geom {
     std::vector<double> views;     // n_views x 12: P (perspective) or Dc, eu, ev, d (parallel)
     std::vector<pyronn::FpRec> fp_rec;
     std::vector<pyronn::BpRec> bp_rec;
+    std::vector<double> views_ext;   // n_views x VIEW64_STRIDE (device copy: d_views64)
 
     // device state (one device per handle)
     std::mutex mu;
@@ -94,6 +113,7 @@ struct pyronn_geom {
     pyronn::FpRec *d_fp = nullptr;
     pyronn::BpRec *d_bp = nullptr;
     int *d_flags = nullptr;
+    double *d_views64 = nullptr;
     void *d_scratch = nullptr;     // FP32 accumulation buffer for reduced-precision adjoints
     size_t scratch_bytes = 0;
     void *d_stage_in = nullptr;    // device buffers of the host-buffer entry points
@@ -103,7 +123,10 @@ struct pyronn_geom {
     int64_t sample_count = -1;     // cached pyronn_geom_count_samples
     pyronn::FpSlabCfg fp_cfg{};    // 0-initialised: chosen on first use
     int fp_cfg_ready = 0;
-    int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged
+    pyronn::FpTmaBox tma_cfg[3] = {};   // per dtype
+    int tma_ready[3] = {0, 0, 0};
+    int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged (thread loads), 3 slab-staged (TMA)
+    int adj_variant = 0;           // 0 auto, 1 atomic scatter, 2 output-stationary bricks
 };
 
 namespace pyronn {
@@ -117,11 +140,14 @@ int finalize_geometry(pyronn_geom *g);          // build FP32 tables from views
 int ensure_device(pyronn_geom *g);               // upload tables to the current device
 OpParams make_params(const pyronn_geom *g, int batch);
 FpSlabCfg choose_fp_slab_cfg(const pyronn_geom *g);
+FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem);
+int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream);
 
 // kernel launchers (return a cudaError_t as int)
 int launch_fp(const OpParams &p, const FpSlabCfg &cfg, const void *vol, void *sino, int dtype, void *stream);
 int launch_fp_direct(const OpParams &p, const void *vol, void *sino, int dtype, void *stream);
 int launch_adjoint(const OpParams &p, const void *sino, void *vol, float *acc32, int dtype, void *stream);
+int launch_adjoint_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp_transpose(const OpParams &p, const void *vol, void *sino, float *acc32, int dtype, void *stream);
 

@@ -163,6 +163,14 @@ class Geometry:
         check(lib().pyronn_geom_read_flags(self._h, out, int(reset)))
         return list(out)
 
+    def fp_config(self, dtype=torch.float32) -> dict:
+        out = (ctypes.c_int * 16)()
+        check(lib().pyronn_geom_fp_config(self._h, _DTYPES[dtype], out))
+        o = list(out)
+        return {"kernel": o[0], "depth": o[1], "guard": o[2], "slab0": o[3],
+                "box": [o[4:7], o[7:10], o[10:13]], "buf_elems": o[13], "smem_bytes": o[14],
+                "thread_box_capacity": o[15]}
+
     def set_variant(self, op: int, variant: int) -> None:
         check(lib().pyronn_geom_set_variant(self._h, int(op), int(variant)))
 

@@ -91,6 +91,9 @@ SMALL = [
                                    sid=60.0, sdd=100.0, vol_offset=(0.8, -0.6, 0.3)), 3),
     Case("helical", dict(kind="cone", vol_shape=(24, 20, 20), vol_spacing=(0.5, 0.5, 0.5), det_shape=(17, 33),
                          det_spacing=(0.6, 0.6), views=17, range=2 * math.pi, sid=75.0, sdd=120.0, pitch=6.0), 3),
+    Case("cone_tma_rows", dict(kind="cone", vol_shape=(19, 23, 32), vol_spacing=(0.45, 0.5, 0.5), det_shape=(21, 35),
+                               det_spacing=(0.55, 0.6), views=10, range=2 * math.pi, sid=70.0, sdd=115.0,
+                               det_offset=(-0.4, 0.9)), 3),
     Case("jittered_positions", dict(kind="positions", vol_shape=(20, 22, 24), vol_spacing=(0.5, 0.5, 0.5),
                                     det_shape=(21, 27), det_spacing=(0.6, 0.6), views=9, range=2 * math.pi,
                                     sid=75.0, sdd=120.0, sigma_mm=0.5, sigma_deg=0.2, seed=5), 3),

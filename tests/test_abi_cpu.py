@@ -128,3 +128,26 @@ def test_step_changes_sample_count(L):
     assert g.count_samples() == 5 * (2 * 20 + 2)     # closed form of the symmetric lattice
     g.step = 0.25
     assert g.count_samples() == 5 * (4 * 20 + 4)
+
+
+@pytest.mark.parametrize("dtype_size,dtype", [(4, "float32"), (2, "bfloat16")])
+def test_fp_config_invariants(L, dtype_size, dtype):
+    """TMA boxes: at most 256 per dimension, x extent a multiple of 16 bytes, first slab plane minus
+    the guard aligned (so x-march boxes start aligned), double buffer within 200 KB."""
+    import torch
+    from paper_2511_08427_gb300.operators import Geometry
+    td = getattr(torch, dtype)
+    g = Geometry.cone_circular((64, 96, 128), (0.5, 0.5, 0.5), (100, 130), (0.6, 0.6), 40, 2 * math.pi, 750.0, 1200.0)
+    c = g.fp_config(td)
+    assert c["kernel"] == 3
+    align = 16 // dtype_size
+    for box in c["box"]:
+        assert all(1 <= e <= 256 for e in box)
+        assert (box[0] * dtype_size) % 16 == 0
+    assert (c["slab0"] - c["guard"]) % align == 0
+    assert c["smem_bytes"] <= 200 * 1024 + 128
+    # rows that are not a multiple of 16 bytes cannot use tensor copies
+    g2 = Geometry.cone_circular((20, 20, 30), (0.5, 0.5, 0.5), (30, 30), (0.6, 0.6), 8, 2 * math.pi, 75.0, 120.0)
+    assert g2.fp_config(td)["kernel"] == 2
+    g2.set_variant(0, 1)
+    assert g2.fp_config(td)["kernel"] == 1
