@@ -186,7 +186,9 @@ PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void 
  * 3 slab-staged kernel filled by TMA tensor copies (needs a row pitch that is a multiple of 16
  * bytes; falls back to 2). op 1 = matched adjoint:
  * variant 0 automatic (= 2), 1 one-thread-per-ray FP32 global atomics, 2 output-stationary
- * bricks accumulated in shared memory. All variants compute the same operator. */
+ * bricks accumulated in shared memory. op 2 = voxel-driven back-projection: variant 0 automatic
+ * (= 2), 1 one thread per voxel in absolute detector coordinates, 2 bricks with detector
+ * coordinates relative to the brick centre's projection. All variants compute the same operator. */
 PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
 
 /* ------------------------------------------------------------------------------------------

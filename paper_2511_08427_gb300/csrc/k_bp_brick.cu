@@ -1,0 +1,215 @@
+// Voxel-driven back-projector, brick form (same operator as bp_direct_kernel, Sec. 2.1).
+//
+// One CTA owns a 16 x 16 x BZ brick; each thread owns one z-column of BZ voxels and keeps its BZ
+// sums in registers over every view. Detector coordinates are formed relative to the projection of
+// the brick centre: per (brick, view), in FP64 (one lane per view of a chunk of 32 views),
+//   (u0, v0, w0)  projection of the brick centre X_b,
+//   Qa = Pa - u0 Pw, Qb = Pb - v0 Pw, Pw   (rows of P times the voxel spacing),
+// so that for a voxel at index offset d from the centre u = u0 + (Qa . d) / w, v = v0 + (Qb . d) / w,
+// w = w0 + Pw . d. Every FP32 quantity is of the size of the brick's footprint, so the bilinear
+// weights carry ~1e-6-pixel errors instead of the ~1e-5 of absolute FP32 detector coordinates.
+// Along the column the three numerators advance by one addition each; when a view's u and w do
+// not depend on z (circular orbits) only v is recomputed.
+#include "device_common.cuh"
+
+namespace pyronn {
+
+constexpr int BPB_X = 16, BPB_Y = 16, BPB_NT = BPB_X * BPB_Y, BPB_CHUNK = 32;
+
+struct BpView {
+    float Qa[3], Qb[3], Pw[3];   // per voxel-index step
+    float w0;                    // depth ratio of the brick centre
+    float fu, fv;                // fractional parts of u0, v0
+    int U0, V0;                  // integer parts of u0, v0
+    int flat;                    // 1: Qa_z == 0 and Pw_z == 0 (u, w constant along z)
+    int valid;                   // 0: the brick centre is at or behind the source plane
+};
+
+__device__ void bp_view_setup(const OpParams &p, int view, const double Xb[3], BpView &o) {
+    const double *x = p.views64 + (size_t)view * VIEW64_STRIDE;
+    const double s[3] = {p.sx, p.sy, p.sz};
+    double Pa[3], Pb[3], Pw[3], a0, b0, w0;
+    if (p.perspective) {
+        for (int i = 0; i < 3; ++i) {
+            Pa[i] = x[i];
+            Pb[i] = x[4 + i];
+            Pw[i] = x[8 + i];
+        }
+        a0 = Pa[0] * Xb[0] + Pa[1] * Xb[1] + Pa[2] * Xb[2] + x[3];
+        b0 = Pb[0] * Xb[0] + Pb[1] * Xb[1] + Pb[2] * Xb[2] + x[7];
+        w0 = Pw[0] * Xb[0] + Pw[1] * Xb[1] + Pw[2] * Xb[2] + x[11];
+    } else {
+        const double *Dc = x, *eu = x + 3, *ev = x + 6;
+        const double hu = 0.5 * (p.det.nu - 1), hv = 0.5 * (p.det.nv - 1);
+        for (int i = 0; i < 3; ++i) {
+            Pa[i] = eu[i] / p.du;
+            Pb[i] = ev[i] / p.dv;
+            Pw[i] = 0.0;
+        }
+        double Y[3] = {Xb[0] - Dc[0], Xb[1] - Dc[1], Xb[2] - Dc[2]};
+        a0 = ((Y[0] * eu[0] + Y[1] * eu[1] + Y[2] * eu[2]) - p.ou) / p.du + hu;
+        b0 = ((Y[0] * ev[0] + Y[1] * ev[1] + Y[2] * ev[2]) - p.ov) / p.dv + hv;
+        w0 = 1.0;
+    }
+    o.valid = w0 > 0.0;
+    if (!o.valid) w0 = 1.0;
+    const double u0 = a0 / w0, v0 = b0 / w0;
+    const double U = floor(u0), Vv = floor(v0);
+    for (int i = 0; i < 3; ++i) {
+        o.Qa[i] = (float)((Pa[i] - u0 * Pw[i]) * s[i]);
+        o.Qb[i] = (float)((Pb[i] - v0 * Pw[i]) * s[i]);
+        o.Pw[i] = (float)(Pw[i] * s[i]);
+    }
+    o.w0 = (float)w0;
+    // clamp the integer parts far outside the detector (such views contribute nothing anyway)
+    const double lim = 4.0e6;
+    o.U0 = (int)fmin(fmax(U, -lim), lim);
+    o.V0 = (int)fmin(fmax(Vv, -lim), lim);
+    o.fu = (float)(u0 - U);
+    o.fv = (float)(v0 - Vv);
+    o.flat = (o.Qa[2] == 0.0f && o.Pw[2] == 0.0f);
+}
+
+// floor and fraction; q is clamped to +-1e6 first (the magic addition needs |q| < 2^22; detector
+// coordinates that far out contribute nothing)
+__device__ __forceinline__ void magic_floor(float q, int &i, float &f) {
+    const float M = 12582912.0f;
+    q = fminf(fmaxf(q, -1.0e6f), 1.0e6f);
+    float t = __fadd_rd(q, M);
+    i = __float_as_int(t) - 0x4B400000;
+    f = q - (t - M);
+}
+
+template <typename T>
+__device__ __forceinline__ float bilerp0(const T *__restrict__ q, int nu, int nv, int iu, int iv, float au, float av) {
+    const bool u0 = (unsigned)iu < (unsigned)nu, u1 = (unsigned)(iu + 1) < (unsigned)nu;
+    const bool v0 = (unsigned)iv < (unsigned)nv, v1 = (unsigned)(iv + 1) < (unsigned)nv;
+    const long long base = (long long)iv * nu + iu;
+    const float q00 = (v0 && u0) ? ldg_f32(q + base) : 0.0f;
+    const float q01 = (v0 && u1) ? ldg_f32(q + base + 1) : 0.0f;
+    const float q10 = (v1 && u0) ? ldg_f32(q + base + nu) : 0.0f;
+    const float q11 = (v1 && u1) ? ldg_f32(q + base + nu + 1) : 0.0f;
+    const float r0 = fmaf(au, q01 - q00, q00);
+    const float r1 = fmaf(au, q11 - q10, q10);
+    return fmaf(av, r1 - r0, r0);
+}
+
+template <typename T, int BZ, bool W2>
+__global__ void __launch_bounds__(BPB_NT) bp_brick_kernel(OpParams p, const T *__restrict__ sino,
+                                                          T *__restrict__ vol) {
+    __shared__ BpView sv[BPB_CHUNK];
+    const int nbz = (p.vol.nz + BZ - 1) / BZ;
+    const int bx0 = blockIdx.x * BPB_X, by0 = blockIdx.y * BPB_Y;
+    const int bz0 = (blockIdx.z % nbz) * BZ;
+    const int b = blockIdx.z / nbz;
+    const int tid = threadIdx.x;
+    const int lx = tid % BPB_X, ly = tid / BPB_X;
+    const int i = bx0 + lx, j = by0 + ly;
+    const T *sb = sino + (long long)b * p.sino_elems;
+    const int nu = p.det.nu, nv = p.det.nv;
+
+    // brick centre relative to the volume centre (world mm) and this thread's offset from it
+    double Xb[3];
+    Xb[0] = (bx0 + 0.5 * (BPB_X - 1) - 0.5 * (p.vol.nx - 1)) * p.sx;
+    Xb[1] = (by0 + 0.5 * (BPB_Y - 1) - 0.5 * (p.vol.ny - 1)) * p.sy;
+    Xb[2] = (bz0 + 0.5 * (BZ - 1) - 0.5 * (p.vol.nz - 1)) * p.sz;
+    const float dx = (float)lx - 0.5f * (BPB_X - 1), dy = (float)ly - 0.5f * (BPB_Y - 1);
+    const float dz0 = -0.5f * (BZ - 1);
+
+    float acc[BZ];
+#pragma unroll
+    for (int z = 0; z < BZ; ++z) acc[z] = 0.0f;
+
+    for (int n0 = 0; n0 < p.n_views; n0 += BPB_CHUNK) {
+        const int nc = min(BPB_CHUNK, p.n_views - n0);
+        __syncthreads();
+        if (tid < nc) bp_view_setup(p, n0 + tid, Xb, sv[tid]);
+        __syncthreads();
+        for (int c = 0; c < nc; ++c) {
+            const BpView &V = sv[c];
+            if (!V.valid) continue;
+            const T *q = sb + (long long)(n0 + c) * nv * nu;
+            float na = fmaf(V.Qa[0], dx, fmaf(V.Qa[1], dy, V.Qa[2] * dz0));
+            float nb = fmaf(V.Qb[0], dx, fmaf(V.Qb[1], dy, V.Qb[2] * dz0));
+            float w = fmaf(V.Pw[0], dx, fmaf(V.Pw[1], dy, fmaf(V.Pw[2], dz0, V.w0)));
+            if (V.flat) {
+                if (!(w > 0.0f)) continue;
+                const float iw = __frcp_rn(w);
+                int iu;
+                float au;
+                magic_floor(fmaf(na, iw, V.fu), iu, au);
+                iu += V.U0;
+                const float om = W2 ? iw * iw : 1.0f;
+#pragma unroll
+                for (int z = 0; z < BZ; ++z) {
+                    int iv;
+                    float av;
+                    magic_floor(fmaf(nb, iw, V.fv), iv, av);
+                    acc[z] = fmaf(om, bilerp0(q, nu, nv, iu, iv + V.V0, au, av), acc[z]);
+                    nb += V.Qb[2];
+                }
+            } else {
+#pragma unroll
+                for (int z = 0; z < BZ; ++z) {
+                    if (w > 0.0f) {
+                        const float iw = __frcp_rn(w);
+                        int iu, iv;
+                        float au, av;
+                        magic_floor(fmaf(na, iw, V.fu), iu, au);
+                        magic_floor(fmaf(nb, iw, V.fv), iv, av);
+                        const float om = W2 ? iw * iw : 1.0f;
+                        acc[z] = fmaf(om, bilerp0(q, nu, nv, iu + V.U0, iv + V.V0, au, av), acc[z]);
+                    }
+                    na += V.Qa[2];
+                    nb += V.Qb[2];
+                    w += V.Pw[2];
+                }
+            }
+        }
+    }
+    if (i < p.vol.nx && j < p.vol.ny) {
+        T *vb = vol + (long long)b * p.vol_elems;
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) {
+            const int k = bz0 + z;
+            if (k < p.vol.nz) vb[((long long)k * p.vol.ny + j) * p.vol.nx + i] = from_f32<T>(acc[z]);
+        }
+    }
+}
+
+template <typename T, int BZ, bool W2>
+static void launch_bpb(const OpParams &p, const void *sino, void *vol, cudaStream_t st) {
+    const int nbx = ceil_div(p.vol.nx, BPB_X), nby = ceil_div(p.vol.ny, BPB_Y), nbz = ceil_div(p.vol.nz, BZ);
+    const int per_launch = 65535 / nbz > 0 ? 65535 / nbz : 1;
+    for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
+        int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
+        dim3 grid(nbx, nby, nbz * nb);
+        bp_brick_kernel<T, BZ, W2><<<grid, BPB_NT, 0, st>>>(p, (const T *)sino + b0 * p.sino_elems,
+                                                           (T *)vol + b0 * p.vol_elems);
+    }
+}
+
+template <typename T>
+static int launch_bpb_t(const OpParams &p, const void *sino, void *vol, cudaStream_t st) {
+    const bool w2 = p.perspective && p.weight == PYRONN_BP_INV_W2;
+    if (p.vol.nz == 1) {
+        if (w2) launch_bpb<T, 1, true>(p, sino, vol, st);
+        else launch_bpb<T, 1, false>(p, sino, vol, st);
+    } else {
+        if (w2) launch_bpb<T, 8, true>(p, sino, vol, st);
+        else launch_bpb<T, 8, false>(p, sino, vol, st);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_bpb_t<float>(p, sino, vol, st);
+        case PYRONN_BF16: return launch_bpb_t<__nv_bfloat16>(p, sino, vol, st);
+        case PYRONN_F16: return launch_bpb_t<__half>(p, sino, vol, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pyronn

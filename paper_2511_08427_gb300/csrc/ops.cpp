@@ -134,10 +134,11 @@ int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out) {
 int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
-    if (op != 0 && op != 1) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
+    if (op < 0 || op > 2) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
     if (variant < 0 || variant > (op == 0 ? 3 : 2)) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
     if (op == 0) g->fp_variant = variant;
-    else g->adj_variant = variant;
+    else if (op == 1) g->adj_variant = variant;
+    else g->bp_variant = variant;
     return PYRONN_OK;
 }
 
@@ -165,7 +166,8 @@ int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch
         return set_error(PYRONN_INVALID_ARG, "unknown back-projection weight %d", weight);
     OpParams p = make_params(g, batch);
     p.weight = weight;
-    return cuda_rc(launch_bp(p, sino, vol, dtype, stream), "back-projection launch");
+    if (g->bp_variant == 1) return cuda_rc(launch_bp(p, sino, vol, dtype, stream), "back-projection launch");
+    return cuda_rc(launch_bp_brick(p, sino, vol, dtype, stream), "back-projection launch");
 }
 
 int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, int weight,

@@ -127,6 +127,7 @@ struct pyronn_geom {
     int tma_ready[3] = {0, 0, 0};
     int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged (thread loads), 3 slab-staged (TMA)
     int adj_variant = 0;           // 0 auto, 1 atomic scatter, 2 output-stationary bricks
+    int bp_variant = 0;            // 0 auto, 1 one thread per voxel (absolute coordinates), 2 bricks
 };
 
 namespace pyronn {
@@ -149,6 +150,7 @@ int launch_fp_direct(const OpParams &p, const void *vol, void *sino, int dtype, 
 int launch_adjoint(const OpParams &p, const void *sino, void *vol, float *acc32, int dtype, void *stream);
 int launch_adjoint_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
+int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp_transpose(const OpParams &p, const void *vol, void *sino, float *acc32, int dtype, void *stream);
 
 size_t dtype_size(int dtype);

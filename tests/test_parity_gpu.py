@@ -85,10 +85,12 @@ def test_adjoint_matches_oracle(ops, case, variant):
     assert rel_l2(a.reshape(ref.shape), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("weight", [0, 1])
 @pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
-def test_bp_matches_oracle(ops, case, weight):
+def test_bp_matches_oracle(ops, case, weight, variant):
     g = case.library_geometry()
+    g.set_variant(2, variant)
     og = case.oracle_geometry()
     for q in (inputs.uniform(og.sino_shape, seed=9), inputs.gaussian(og.sino_shape, seed=10)):
         b = host(ops.back_project(to_dev(q.reshape((og.n_views, -1)) if case.ndim == 2 else q), g, weight))
