@@ -173,6 +173,19 @@ PYRONN_API int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype
 PYRONN_API int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, int weight,
                                    void *stream);
 
+/* Matched adjoint that allocates no device memory (the paper has no counterpart: this is a
+ * deployment variant of pyronn_adjoint's one-thread-per-ray atomic scatter). For callers that
+ * cannot let a library call cudaMalloc, for example code running inside a memory pool that owns
+ * the device or a pipeline that must not allocate after start-up. The per-view ray table and the
+ * FP32 accumulator live in fixed device arrays of the library (at most 4096 views and 8M voxels
+ * in total, volume x batch: 32 MiB), held by every GPU that loads the library until the process
+ * exits; larger requests return PYRONN_INVALID_ARG. The first call on a device looks up the
+ * arrays' device addresses (make it before any stream capture). Calls share the arrays: each call
+ * clears the accumulator first, and calls that overlap on the GPU race, so serialise them.
+ * Same arguments and result as pyronn_adjoint (vol is overwritten); asynchronous on stream. */
+PYRONN_API int pyronn_adjoint_noalloc(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch,
+                                      void *stream);
+
 /* Host-buffer variants: copy the input from host memory (pinned for best speed) into device
  * buffers owned by the geometry (allocated on first use), run the operator on `stream`, copy
  * the result back and synchronise the stream. */

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("pyronn_adjoint", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_bp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_bp_transpose", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
+    ("pyronn_adjoint_noalloc", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_fp_host", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_adjoint_host", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_geom_read_flags", _c_int, [_vp, ctypes.POINTER(_c_int), _c_int]),

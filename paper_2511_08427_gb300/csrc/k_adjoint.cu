@@ -79,6 +79,35 @@ static int launch_t(const OpParams &p, const void *sino, float *acc, void *vol, 
     return (int)cudaGetLastError();
 }
 
+// Scatter into the caller-provided FP32 buffer acc (zeroed here), then write vol from it.
+template <typename T>
+static int launch_via_acc_t(const OpParams &p, const void *sino, float *acc, void *vol, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)p.vol_elems * p.batch, st);
+    if (e != cudaSuccess) return (int)e;
+    dim3 block(32, 8);
+    const int per_launch = 65535 / p.n_views > 0 ? 65535 / p.n_views : 1;
+    for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
+        int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
+        dim3 grid(ceil_div(p.det.nu, 32), ceil_div(p.det.nv, 8), p.n_views * nb);
+        adjoint_scatter_kernel<T><<<grid, block, 0, st>>>(p, (const T *)sino + b0 * p.sino_elems,
+                                                          acc + b0 * p.vol_elems);
+    }
+    long long n = p.vol_elems * p.batch;
+    int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    convert_from_f32_kernel<T><<<blocks, 256, 0, st>>>(acc, (T *)vol, n);
+    return (int)cudaGetLastError();
+}
+
+int launch_adjoint_scatter_acc(const OpParams &p, const void *sino, float *acc, void *vol, int dtype, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_via_acc_t<float>(p, sino, acc, vol, st);
+        case PYRONN_BF16: return launch_via_acc_t<__nv_bfloat16>(p, sino, acc, vol, st);
+        case PYRONN_F16: return launch_via_acc_t<__half>(p, sino, acc, vol, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
 int launch_adjoint(const OpParams &p, const void *sino, void *vol, float *acc32, int dtype, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     switch (dtype) {

@@ -149,6 +149,7 @@ int launch_fp(const OpParams &p, const FpSlabCfg &cfg, const void *vol, void *si
 int launch_fp_direct(const OpParams &p, const void *vol, void *sino, int dtype, void *stream);
 int launch_adjoint(const OpParams &p, const void *sino, void *vol, float *acc32, int dtype, void *stream);
 int launch_adjoint_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
+int launch_adjoint_scatter_acc(const OpParams &p, const void *sino, float *acc, void *vol, int dtype, void *stream);
 int launch_bp(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp_transpose(const OpParams &p, const void *vol, void *sino, float *acc32, int dtype, void *stream);
