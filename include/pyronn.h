@@ -186,6 +186,35 @@ PYRONN_API int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino,
 PYRONN_API int pyronn_adjoint_noalloc(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch,
                                       void *stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Batched plans: many volumes, each with its own size and geometry, in one persistent launch per
+ * operator (the paper's layers carry a batch dimension, Listing 1; here every batch member may
+ * have its own geometry). Each CTA takes (view, detector tile) items (forward projection) or
+ * volume-brick items (adjoint, back-projection) from a device work counter, largest items first.
+ * Every call is one cudaMemsetAsync of the counter plus one kernel launch on `stream` and
+ * allocates nothing, so calls can be captured in a CUDA graph; the plan is created (and the
+ * geometries' device tables uploaded) before capture.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct pyronn_plan *pyronn_plan_t;
+
+/* n (1..16) 3D geometries; dtype is the storage type of every buffer used with the plan. Volumes
+ * whose rows (Nx elements) are not a multiple of 16 bytes cannot use tensor copies: their forward
+ * projection runs as a separate per-geometry launch on the same stream. The plan refers to the
+ * geometries (it does not own them): keep them alive while the plan is used. */
+PYRONN_API int pyronn_plan_create(int n, const pyronn_geom_t *geoms, int dtype, pyronn_plan_t *out);
+PYRONN_API int pyronn_plan_destroy(pyronn_plan_t plan);
+
+/* Item counts and persistent grid sizes: grids[3] = {forward, adjoint, back-projection}. */
+PYRONN_API int pyronn_plan_info(pyronn_plan_t plan, int *n, int64_t *items_fp, int64_t *items_brick, int *grids);
+
+/* vols / sinos: host arrays of n device pointers, in the order of the geometries given to
+ * pyronn_plan_create. Same operators and overwrite semantics as pyronn_fp / pyronn_adjoint /
+ * pyronn_bp with batch = 1 per geometry. */
+PYRONN_API int pyronn_plan_fp(pyronn_plan_t plan, const void *const *vols, void *const *sinos, void *stream);
+PYRONN_API int pyronn_plan_adjoint(pyronn_plan_t plan, const void *const *sinos, void *const *vols, void *stream);
+PYRONN_API int pyronn_plan_bp(pyronn_plan_t plan, const void *const *sinos, void *const *vols, int weight,
+                              void *stream);
+
 /* Host-buffer variants: copy the input from host memory (pinned for best speed) into device
  * buffers owned by the geometry (allocated on first use), run the operator on `stream`, copy
  * the result back and synchronise the stream. */
@@ -203,6 +232,14 @@ PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void 
  * (= 2), 1 one thread per voxel in absolute detector coordinates, 2 bricks with detector
  * coordinates relative to the brick centre's projection. All variants compute the same operator. */
 PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
+
+/* Tuning knobs of the kernels (used by the autotuner; 0 restores the automatic choice). All
+ * settings compute the same operator. PYRONN_TUNE_FP_DEPTH: slab depth of the TMA-staged forward
+ * projector in voxel planes (rounded up to the 16-byte x alignment); PYRONN_TUNE_FP_BUFFERS: 1 or
+ * 2 shared-memory slab buffers (2 overlaps the next copy with sampling; 1 halves shared memory so
+ * more CTAs fit on an SM). */
+typedef enum { PYRONN_TUNE_FP_DEPTH = 0, PYRONN_TUNE_FP_BUFFERS = 1 } pyronn_tuning_param;
+PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
 
 /* ------------------------------------------------------------------------------------------
  * Diagnostics.

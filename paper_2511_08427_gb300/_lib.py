@@ -54,11 +54,19 @@ SIGNATURES = [
     ("pyronn_geom_get_views", _c_int, [_vp, _dp]),
     ("pyronn_geom_count_samples", _c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
     ("pyronn_geom_set_variant", _c_int, [_vp, _c_int, _c_int]),
+    ("pyronn_geom_set_tuning", _c_int, [_vp, _c_int, _c_int]),
     ("pyronn_fp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_adjoint", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_bp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_bp_transpose", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_adjoint_noalloc", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
+    ("pyronn_plan_create", _c_int, [_c_int, ctypes.POINTER(ctypes.c_void_p), _c_int, _geomp]),
+    ("pyronn_plan_destroy", _c_int, [_vp]),
+    ("pyronn_plan_info", _c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_int)]),
+    ("pyronn_plan_fp", _c_int, [_vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), _vp]),
+    ("pyronn_plan_adjoint", _c_int, [_vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), _vp]),
+    ("pyronn_plan_bp", _c_int, [_vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), _c_int, _vp]),
     ("pyronn_fp_host", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_adjoint_host", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_geom_read_flags", _c_int, [_vp, ctypes.POINTER(_c_int), _c_int]),

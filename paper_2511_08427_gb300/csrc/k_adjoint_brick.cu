@@ -38,6 +38,39 @@ struct BrickView {
 
 constexpr int ADJ_VIEW_CHUNK = 32;
 
+// floor / fraction by the round-down magic-number addition; q is clamped to +-64 (brick-local
+// positions of in-brick samples are within [-1, 16]; anything beyond contributes nothing)
+__device__ __forceinline__ void floor_frac_clamped(float q, int &i, float &f) {
+    const float M = 12582912.0f;
+    q = fminf(fmaxf(q, -64.0f), 64.0f);
+    const float t = __fadd_rd(q, M);
+    i = __float_as_int(t) - 0x4B400000;
+    f = q - (t - M);
+}
+
+__device__ __forceinline__ void red_add_shared(unsigned addr, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// add the eight corner weights of cell (ix, iy, iz) to the brick accumulator (corners inside only)
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ void flush_cell(unsigned acc_base, int ix, int iy, int iz, float a0, float a1, float a2,
+                                           float a3, float a4, float a5, float a6, float a7) {
+    const bool x0 = (unsigned)ix < (unsigned)BX, x1 = (unsigned)(ix + 1) < (unsigned)BX;
+    const bool y0 = (unsigned)iy < (unsigned)BY, y1 = (unsigned)(iy + 1) < (unsigned)BY;
+    const bool z0 = (unsigned)iz < (unsigned)BZ, z1 = (unsigned)(iz + 1) < (unsigned)BZ;
+    const unsigned base = acc_base + 4u * (unsigned)((iz * BY + iy) * BX + ix);
+    constexpr unsigned SY = 4u * BX, SZ = 4u * BX * BY;
+    if (z0 && y0 && x0) red_add_shared(base, a0);
+    if (z0 && y0 && x1) red_add_shared(base + 4u, a1);
+    if (z0 && y1 && x0) red_add_shared(base + SY, a2);
+    if (z0 && y1 && x1) red_add_shared(base + SY + 4u, a3);
+    if (z1 && y0 && x0) red_add_shared(base + SZ, a4);
+    if (z1 && y0 && x1) red_add_shared(base + SZ + 4u, a5);
+    if (z1 && y1 && x0) red_add_shared(base + SZ + SY, a6);
+    if (z1 && y1 && x1) red_add_shared(base + SZ + SY + 4u, a7);
+}
+
 // FP64 per-(brick, view) set-up. Xb: brick centre relative to the volume centre (world mm);
 // ext_lo / ext_hi: the extended brick (one voxel around it) relative to the volume centre.
 __device__ void brick_view_setup(const OpParams &p, int view, const double Xb[3], const double ext_lo[3],
@@ -133,23 +166,31 @@ __device__ void brick_view_setup(const OpParams &p, int view, const double Xb[3]
     bv.f = (float)(T - K);
 }
 
+template <int BX, int BY, int BZ>
+struct AdjShared {
+    float acc[BX * BY * BZ];
+    BrickView sv[ADJ_VIEW_CHUNK];
+    int s_off[ADJ_VIEW_CHUNK + 1];
+};
+
+// Adjoint of one brick (block indices bxi, byi, bzi) of volume b: accumulates every view in shared
+// memory and writes the brick once.
 template <typename T, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(256, 4) adjoint_brick_kernel(OpParams p, const T *__restrict__ sino,
-                                                            T *__restrict__ vol) {
+__device__ __forceinline__ void adjoint_brick(const OpParams &p, const T *__restrict__ sino, T *__restrict__ vol,
+                                              int bxi, int byi, int bzi, int b, AdjShared<BX, BY, BZ> &S) {
     constexpr int NT = 256;
     constexpr int NB = BX * BY * BZ;
-    __shared__ float acc[NB];
-    __shared__ BrickView sv[ADJ_VIEW_CHUNK];
-    __shared__ int s_off[ADJ_VIEW_CHUNK + 1];
-
-    const int nbz = (p.vol.nz + BZ - 1) / BZ;
-    const int bx0 = blockIdx.x * BX, by0 = blockIdx.y * BY;
-    const int bz0 = (blockIdx.z % nbz) * BZ;
-    const int b = blockIdx.z / nbz;
+    float *acc = S.acc;
+    BrickView *sv = S.sv;
+    int *s_off = S.s_off;
+    const int bx0 = bxi * BX, by0 = byi * BY;
+    const int bz0 = bzi * BZ;
     const int tid = threadIdx.x;
     const T *sb = sino + (long long)b * p.sino_elems;
 
+    __syncthreads();   // the previous brick's write-back is done with the accumulator
     for (int i = tid; i < NB; i += NT) acc[i] = 0.0f;
+    const unsigned acc_base = (unsigned)__cvta_generic_to_shared(acc);
 
     // brick centre and extended brick, relative to the volume centre (world mm)
     const double sp[3] = {p.sx, p.sy, p.sz};
@@ -174,10 +215,12 @@ __global__ void __launch_bounds__(256, 4) adjoint_brick_kernel(OpParams p, const
         if (tid < nc) brick_view_setup(p, n0 + tid, Xb, elo, ehi, sv[tid]);
         __syncthreads();
         if (tid == 0) {
+            // rectangles padded to multiples of 3: rays are visited in nine interleaved 3 x 3 phases,
+            // so the rays of consecutive lanes are 3 pixels apart and rarely share a voxel
             int o = 0;
             for (int c = 0; c < nc; ++c) {
                 s_off[c] = o;
-                o += sv[c].nu_r * sv[c].nv_r;
+                o += 9 * ((sv[c].nu_r + 2) / 3) * ((sv[c].nv_r + 2) / 3);
             }
             s_off[nc] = o;
         }
@@ -188,7 +231,12 @@ __global__ void __launch_bounds__(256, 4) adjoint_brick_kernel(OpParams p, const
             while (r >= s_off[c + 1]) ++c;
             const BrickView &V = sv[c];
             const int lr = r - s_off[c];
-            const int du_ = lr % V.nu_r, dv_ = lr / V.nu_r;
+            const int nu3 = (V.nu_r + 2) / 3, nv3 = (V.nv_r + 2) / 3;
+            const int cls = nu3 * nv3;
+            const int ph = lr / cls, qq = lr - ph * cls;
+            const int dv3 = qq / nu3;
+            const int du_ = (ph % 3) + 3 * (qq - dv3 * nu3), dv_ = (ph / 3) + 3 * dv3;
+            if (du_ >= V.nu_r || dv_ >= V.nv_r) continue;
             const int u = V.u_lo + du_, v = V.v_lo + dv_;
             float y = ldg_f32(sb + ((long long)(n0 + c) * nv + v) * nu + u);
             if (y == 0.0f) continue;
@@ -228,26 +276,39 @@ __global__ void __launch_bounds__(256, 4) adjoint_brick_kernel(OpParams p, const
             const float idt = 1.0f / dt;
             const int j0 = (int)floorf((slo - c_r) * idt);
             const int j1 = (int)ceilf((shi - c_r) * idt);
-            for (int j = j0; j <= j1; ++j) {
-                const float s = fmaf((float)j, dt, c_r);
-                const float qx = fmaf(s, qd0, qP0), qy = fmaf(s, qd1, qP1), qz = fmaf(s, qd2, qP2);
-                const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
-                const float ax = qx - fx, ay = qy - fy, az = qz - fz;
-                const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-                const bool x0 = (unsigned)ix < (unsigned)BX, x1 = (unsigned)(ix + 1) < (unsigned)BX;
-                const bool y0 = (unsigned)iy < (unsigned)BY, y1 = (unsigned)(iy + 1) < (unsigned)BY;
-                const bool z0 = (unsigned)iz < (unsigned)BZ, z1 = (unsigned)(iz + 1) < (unsigned)BZ;
-                const float wz1 = y * az, wz0 = y - wz1;
-                const float w00 = wz0 * (1.0f - ay), w01 = wz0 * ay, w10 = wz1 * (1.0f - ay), w11 = wz1 * ay;
-                const int base = (iz * BY + iy) * BX + ix;
-                if (z0 && y0 && x0) atomicAdd(acc + base, w00 * (1.0f - ax));
-                if (z0 && y0 && x1) atomicAdd(acc + base + 1, w00 * ax);
-                if (z0 && y1 && x0) atomicAdd(acc + base + BX, w01 * (1.0f - ax));
-                if (z0 && y1 && x1) atomicAdd(acc + base + BX + 1, w01 * ax);
-                if (z1 && y0 && x0) atomicAdd(acc + base + BX * BY, w10 * (1.0f - ax));
-                if (z1 && y0 && x1) atomicAdd(acc + base + BX * BY + 1, w10 * ax);
-                if (z1 && y1 && x0) atomicAdd(acc + base + BX * BY + BX, w11 * (1.0f - ax));
-                if (z1 && y1 && x1) atomicAdd(acc + base + BX * BY + BX + 1, w11 * ax);
+            // the eight weights accumulate in registers while the sample stays in one cell and are
+            // flushed to the brick (no-return shared-memory reductions) when it moves on
+            float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f, a4 = 0.0f, a5 = 0.0f, a6 = 0.0f, a7 = 0.0f;
+            int pix = 0, piy = 0, piz = 0, pkey = -1;
+            for (int j = j0; j <= j1 + 1; ++j) {
+                int key = -2, ix = 0, iy = 0, iz = 0;
+                float ax = 0.0f, ay = 0.0f, az = 0.0f;
+                if (j <= j1) {
+                    const float s = fmaf((float)j, dt, c_r);
+                    const float qx = fmaf(s, qd0, qP0), qy = fmaf(s, qd1, qP1), qz = fmaf(s, qd2, qP2);
+                    floor_frac_clamped(qx, ix, ax);
+                    floor_frac_clamped(qy, iy, ay);
+                    floor_frac_clamped(qz, iz, az);
+                    key = ((iz + 8) << 20) | ((iy + 8) << 10) | (ix + 8);
+                }
+                if (key != pkey) {
+                    if (pkey >= 0) flush_cell<BX, BY, BZ>(acc_base, pix, piy, piz, a0, a1, a2, a3, a4, a5, a6, a7);
+                    a0 = a1 = a2 = a3 = a4 = a5 = a6 = a7 = 0.0f;
+                    pkey = key;
+                    pix = ix; piy = iy; piz = iz;
+                }
+                if (j <= j1) {
+                    const float wz1 = y * az, wz0 = y - wz1;
+                    const float w00 = wz0 * (1.0f - ay), w01 = wz0 * ay, w10 = wz1 * (1.0f - ay), w11 = wz1 * ay;
+                    a0 = fmaf(w00, 1.0f - ax, a0);
+                    a1 = fmaf(w00, ax, a1);
+                    a2 = fmaf(w01, 1.0f - ax, a2);
+                    a3 = fmaf(w01, ax, a3);
+                    a4 = fmaf(w10, 1.0f - ax, a4);
+                    a5 = fmaf(w10, ax, a5);
+                    a6 = fmaf(w11, 1.0f - ax, a6);
+                    a7 = fmaf(w11, ax, a7);
+                }
             }
         }
     }
@@ -258,6 +319,35 @@ __global__ void __launch_bounds__(256, 4) adjoint_brick_kernel(OpParams p, const
         const int gx = bx0 + lx, gy = by0 + ly, gz = bz0 + lz;
         if (gx < p.vol.nx && gy < p.vol.ny && gz < p.vol.nz)
             vb[((long long)gz * p.vol.ny + gy) * p.vol.nx + gx] = from_f32<T>(acc[i]);
+    }
+}
+
+template <typename T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(256, 4) adjoint_brick_kernel(OpParams p, const T *__restrict__ sino,
+                                                            T *__restrict__ vol) {
+    __shared__ AdjShared<BX, BY, BZ> S;
+    const int nbz = (p.vol.nz + BZ - 1) / BZ;
+    adjoint_brick<T, BX, BY, BZ>(p, sino, vol, blockIdx.x, blockIdx.y, blockIdx.z % nbz, blockIdx.z / nbz, S);
+}
+
+// Persistent launch over the bricks of several volumes (items = bricks, largest volumes first).
+template <typename T, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(256, 4) adjoint_brick_batched_kernel(const __grid_constant__ PlanLaunch L) {
+    __shared__ AdjShared<BX, BY, BZ> S;
+    __shared__ int s_item;
+    const long long total = L.item_end[L.n - 1];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(L.counter, 1);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int i = 0;
+        while (item >= L.item_end[i]) ++i;
+        const PlanVolume &V = L.v[i];
+        const int local = (int)(item - (i ? L.item_end[i - 1] : 0));
+        const int bxi = local % V.ntx, byi = (local / V.ntx) % V.nty, bzi = local / (V.ntx * V.nty);
+        adjoint_brick<T, BX, BY, BZ>(V.p, (const T *)V.in, (T *)V.out, bxi, byi, bzi, 0, S);
     }
 }
 
@@ -278,6 +368,30 @@ template <typename T>
 static int launch_brick_dims(const OpParams &p, const void *sino, void *vol, cudaStream_t st) {
     if (p.vol.nz == 1) return launch_brick_t<T, 32, 32, 1>(p, sino, vol, st);
     return launch_brick_t<T, 16, 16, 16>(p, sino, vol, st);
+}
+
+template <typename T>
+static int launch_adj_batched_t(const PlanLaunch &L, int grid, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return (int)e;
+    adjoint_brick_batched_kernel<T, 16, 16, 16><<<grid, 256, 0, st>>>(L);
+    return (int)cudaGetLastError();
+}
+
+// bricks of the batched adjoint are 16^3 (3D volumes only)
+int launch_adjoint_brick_batched(const PlanLaunch &L, int dtype, int grid, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_adj_batched_t<float>(L, grid, st);
+        case PYRONN_BF16: return launch_adj_batched_t<__nv_bfloat16>(L, grid, st);
+        case PYRONN_F16: return launch_adj_batched_t<__half>(L, grid, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int adjoint_brick_batched_occupancy(int *blocks_per_sm) {
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                              adjoint_brick_batched_kernel<float, 16, 16, 16>, 256, 0);
 }
 
 int launch_adjoint_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream) {

@@ -94,14 +94,12 @@ __device__ __forceinline__ float bilerp0(const T *__restrict__ q, int nu, int nv
     return fmaf(av, r1 - r0, r0);
 }
 
+// Back-projection of one brick (block indices bxi, byi, bzi) of volume b.
 template <typename T, int BZ, bool W2>
-__global__ void __launch_bounds__(BPB_NT) bp_brick_kernel(OpParams p, const T *__restrict__ sino,
-                                                          T *__restrict__ vol) {
-    __shared__ BpView sv[BPB_CHUNK];
-    const int nbz = (p.vol.nz + BZ - 1) / BZ;
-    const int bx0 = blockIdx.x * BPB_X, by0 = blockIdx.y * BPB_Y;
-    const int bz0 = (blockIdx.z % nbz) * BZ;
-    const int b = blockIdx.z / nbz;
+__device__ __forceinline__ void bp_brick(const OpParams &p, const T *__restrict__ sino, T *__restrict__ vol, int bxi,
+                                         int byi, int bzi, int b, BpView *sv) {
+    const int bx0 = bxi * BPB_X, by0 = byi * BPB_Y;
+    const int bz0 = bzi * BZ;
     const int tid = threadIdx.x;
     const int lx = tid % BPB_X, ly = tid / BPB_X;
     const int i = bx0 + lx, j = by0 + ly;
@@ -178,6 +176,36 @@ __global__ void __launch_bounds__(BPB_NT) bp_brick_kernel(OpParams p, const T *_
 }
 
 template <typename T, int BZ, bool W2>
+__global__ void __launch_bounds__(BPB_NT) bp_brick_kernel(OpParams p, const T *__restrict__ sino,
+                                                          T *__restrict__ vol) {
+    __shared__ BpView sv[BPB_CHUNK];
+    const int nbz = (p.vol.nz + BZ - 1) / BZ;
+    bp_brick<T, BZ, W2>(p, sino, vol, blockIdx.x, blockIdx.y, blockIdx.z % nbz, blockIdx.z / nbz, sv);
+}
+
+// Persistent launch over the bricks of several volumes.
+template <typename T, bool W2>
+__global__ void __launch_bounds__(BPB_NT) bp_brick_batched_kernel(const __grid_constant__ PlanLaunch L) {
+    __shared__ BpView sv[BPB_CHUNK];
+    __shared__ int s_item;
+    const long long total = L.item_end[L.n - 1];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(L.counter, 1);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int i = 0;
+        while (item >= L.item_end[i]) ++i;
+        const PlanVolume &V = L.v[i];
+        const int local = (int)(item - (i ? L.item_end[i - 1] : 0));
+        const int bxi = local % V.ntx, byi = (local / V.ntx) % V.nty, bzi = local / (V.ntx * V.nty);
+        if (W2 && V.p.perspective) bp_brick<T, 8, true>(V.p, (const T *)V.in, (T *)V.out, bxi, byi, bzi, 0, sv);
+        else bp_brick<T, 8, false>(V.p, (const T *)V.in, (T *)V.out, bxi, byi, bzi, 0, sv);
+    }
+}
+
+template <typename T, int BZ, bool W2>
 static void launch_bpb(const OpParams &p, const void *sino, void *vol, cudaStream_t st) {
     const int nbx = ceil_div(p.vol.nx, BPB_X), nby = ceil_div(p.vol.ny, BPB_Y), nbz = ceil_div(p.vol.nz, BZ);
     const int per_launch = 65535 / nbz > 0 ? 65535 / nbz : 1;
@@ -200,6 +228,31 @@ static int launch_bpb_t(const OpParams &p, const void *sino, void *vol, cudaStre
         else launch_bpb<T, 8, false>(p, sino, vol, st);
     }
     return (int)cudaGetLastError();
+}
+
+template <typename T>
+static int launch_bp_batched_t(const PlanLaunch &L, int weight, int grid, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return (int)e;
+    if (weight == PYRONN_BP_INV_W2) bp_brick_batched_kernel<T, true><<<grid, BPB_NT, 0, st>>>(L);
+    else bp_brick_batched_kernel<T, false><<<grid, BPB_NT, 0, st>>>(L);
+    return (int)cudaGetLastError();
+}
+
+// bricks of the batched back-projection are 16 x 16 x 8 (3D volumes only)
+int launch_bp_brick_batched(const PlanLaunch &L, int dtype, int weight, int grid, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_bp_batched_t<float>(L, weight, grid, st);
+        case PYRONN_BF16: return launch_bp_batched_t<__nv_bfloat16>(L, weight, grid, st);
+        case PYRONN_F16: return launch_bp_batched_t<__half>(L, weight, grid, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int bp_brick_batched_occupancy(int *blocks_per_sm) {
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bp_brick_batched_kernel<float, true>,
+                                                              BPB_NT, 0);
 }
 
 int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream) {

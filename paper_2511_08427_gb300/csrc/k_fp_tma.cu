@@ -84,23 +84,24 @@ struct SlabBox {
     bool fits;      // the tile's footprint in this slab fits the box
 };
 
-template <typename T>
-__global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox cfg,
-                                                           const __grid_constant__ TmaMaps maps,
-                                                           const T *__restrict__ vol, T *__restrict__ sino) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // TMA destinations: 128-byte aligned by construction (the launch adds 128 bytes of slack)
-    const unsigned raw_u32 = smem_u32(smem_raw);
-    const unsigned pad = ((raw_u32 + 127u) & ~127u) - raw_u32;
-    T *const buf0 = (T *)(smem_raw + pad);
-    T *const buf1 = (T *)(smem_raw + pad + sizeof(T) * (size_t)cfg.buf_elems);
-    __shared__ __align__(8) unsigned long long s_bar[2];
-    __shared__ float s_corner[5][6];
-    __shared__ int s_srange[2];
+struct FpTmaShared {
+    unsigned long long bar[2];
+    float corner[5][6];
+    int srange[2];
+};
 
-    const int view = blockIdx.z % p.n_views;
-    const int b = blockIdx.z / p.n_views;
-    const int tu0 = blockIdx.x * TMA_TU, tv0 = blockIdx.y * TMA_TV;
+// One detector tile (tile_x, tile_y) of one view of volume b: returns false if a tensor copy was lost
+// (the CTA must stop). bars / ph: the CTA's two slab mbarriers and the number of loads already
+// consumed on each (the wait parity), carried across tiles by persistent launches.
+template <typename T>
+__device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &cfg, const CUtensorMap *maps3,
+                                            const T *__restrict__ vol, T *__restrict__ sino, int view, int b,
+                                            int tile_x, int tile_y, T *const buf0, T *const buf1, FpTmaShared &sh,
+                                            unsigned ph[2]) {
+    const bool dbl = cfg.nbuf == 2;
+    float (*s_corner)[6] = sh.corner;
+    int *s_srange = sh.srange;
+    const int tu0 = tile_x * TMA_TU, tv0 = tile_y * TMA_TV;
     const int tu1 = min(tu0 + TMA_TU, p.det.nu) - 1, tv1 = min(tv0 + TMA_TV, p.det.nv) - 1;
     const int tid = threadIdx.x;
     const int u = tu0 + tid % TMA_TU, v = tv0 + tid / TMA_TU;
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
     const FpRec &rec = p.fp[view];
     const T *vb = vol + (long long)b * p.vol_elems;
 
+    __syncthreads();   // the previous tile's readers of the shared corner rays are done
     if (tid < 5) {
         float cu, cv;
         if (tid < 4) {
@@ -124,9 +126,6 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
     if (tid == 0) {
         s_srange[0] = 1 << 30;
         s_srange[1] = -(1 << 30);
-        mbar_init(smem_u32(&s_bar[0]), 1);
-        mbar_init(smem_u32(&s_bar[1]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     RayIdx r = ray_setup(rec, p.vol, (float)min(u, tu1), (float)min(v, tv1));
     int k0 = 0, k1 = -1;
@@ -154,7 +153,7 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
     const int BXb = cfg.bx[m], BYb = cfg.by[m], BZb = cfg.bz[m];
     const int box_elems = BXb * BYb * BZb;
     const unsigned box_bytes = (unsigned)(sizeof(T) * box_elems);
-    const CUtensorMap *tmap = &maps.map[m];
+    const CUtensorMap *tmap = &maps3[m];
 
     // slab range of this tile: union of the rays' in-box sample ranges
     if (hit) {
@@ -170,7 +169,7 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
     __syncthreads();
     const int s_first = s_srange[0], s_last = s_srange[1];
     const int nsl = s_last >= s_first ? s_last - s_first + 1 : 0;
-    const unsigned bars[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    const unsigned bars[2] = {smem_u32(&sh.bar[0]), smem_u32(&sh.bar[1])};
     const int align = 16 / (int)sizeof(T);
 
     // box of slab s (uniform across the CTA)
@@ -220,24 +219,26 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
         }
         for (int i = 0; i < nsl; ++i) {
             const int s = s_first + i;
-            const int bi = i & 1;
-            if (tid == 0 && i + 1 < nsl) {
+            const int bi = dbl ? (i & 1) : 0;
+            const unsigned parity = ph[bi] & 1u;
+            if (dbl && tid == 0 && i + 1 < nsl) {
                 SlabBox sbn = slab_box(s + 1);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(bars[bi ^ 1], box_bytes);
                 tma_load_4d(smem_u32(bi ? buf0 : buf1), tmap, bars[bi ^ 1], sbn.lo[0], sbn.lo[1], sbn.lo[2], b);
             }
             const SlabBox sb = slab_box(s);
-            bool ok = mbar_wait_bounded(bars[bi], (unsigned)((i >> 1) & 1));
+            bool ok = mbar_wait_bounded(bars[bi], parity);
             // a copy lost anywhere aborts every CTA at its next slab, so the launch ends promptly
             if (tid == 0 && *(volatile int *)(p.flags + FLAG_TMA_TIMEOUT) != 0) ok = false;
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) atomicAdd(p.flags + FLAG_TMA_TIMEOUT, 1);
                 // wait (bounded) for the copies still in flight before the shared memory goes away
-                mbar_wait_bounded(bars[bi], (unsigned)((i >> 1) & 1));
-                if (i + 1 < nsl) mbar_wait_bounded(bars[bi ^ 1], (unsigned)(((i + 1) >> 1) & 1));
-                return;
+                mbar_wait_bounded(bars[bi], parity);
+                if (dbl && i + 1 < nsl) mbar_wait_bounded(bars[bi ^ 1], ph[bi ^ 1] & 1u);
+                return false;
             }
+            ++ph[bi];
             const int b_lo = base0 + s * D;
             const int b_hi = min(b_lo + D, Nm);
             int ka = 0, kb = -1;
@@ -262,6 +263,11 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
                 const float c0z = fmaf(hdt, r.dz, r.cz - (float)sb.lo[2]);
                 const float stx = p.dt * r.dx, sty = p.dt * r.dy, stz = p.dt * r.dz;
                 float kf = (float)ka;
+                // the eight corner values stay in registers while consecutive samples share a cell;
+                // lanes that keep their cell issue no shared-memory reads
+                int pbase = -1;
+                float v000 = 0.0f, v001 = 0.0f, v010 = 0.0f, v011 = 0.0f;
+                float v100 = 0.0f, v101 = 0.0f, v110 = 0.0f, v111 = 0.0f;
                 for (int k = ka; k <= kb; ++k, kf += 1.0f) {
                     const float qx = fmaf(kf, stx, c0x), qy = fmaf(kf, sty, c0y), qz = fmaf(kf, stz, c0z);
                     int ix, iy, iz;
@@ -274,13 +280,17 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
                         atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
                         acc += trilerp_zero(vb, p.vol, qx + (float)sb.lo[0], qy + (float)sb.lo[1],
                                             qz + (float)sb.lo[2]);
+                        pbase = -1;
                         continue;
                     }
-                    const T *s0 = box + base;
-                    const float v000 = to_f32(s0[0]), v001 = to_f32(s0[1]);
-                    const float v010 = to_f32(s0[sy]), v011 = to_f32(s0[sy + 1]);
-                    const float v100 = to_f32(s0[sz]), v101 = to_f32(s0[sz + 1]);
-                    const float v110 = to_f32(s0[sz + sy]), v111 = to_f32(s0[sz + sy + 1]);
+                    if (base != pbase) {
+                        const T *s0 = box + base;
+                        v000 = to_f32(s0[0]); v001 = to_f32(s0[1]);
+                        v010 = to_f32(s0[sy]); v011 = to_f32(s0[sy + 1]);
+                        v100 = to_f32(s0[sz]); v101 = to_f32(s0[sz + 1]);
+                        v110 = to_f32(s0[sz + sy]); v111 = to_f32(s0[sz + sy + 1]);
+                        pbase = base;
+                    }
                     const float c00 = fmaf(ax, v001 - v000, v000);
                     const float c01 = fmaf(ax, v011 - v010, v010);
                     const float c10 = fmaf(ax, v101 - v100, v100);
@@ -296,7 +306,13 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
                     acc += trilerp_zero(vb, p.vol, fmaf(t, r.dx, r.cx), fmaf(t, r.dy, r.cy), fmaf(t, r.dz, r.cz));
                 }
             }
-            __syncthreads();   // everyone is done with buf[bi] before it is refilled
+            __syncthreads();   // everyone is done with this buffer before it is refilled
+            if (!dbl && tid == 0 && i + 1 < nsl) {
+                SlabBox sbn = slab_box(s + 1);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(bars[0], box_bytes);
+                tma_load_4d(smem_u32(buf0), tmap, bars[0], sbn.lo[0], sbn.lo[1], sbn.lo[2], b);
+            }
         }
     }
     if (direct_ray) {
@@ -308,6 +324,73 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox 
     }
     if (active)
         sino[(long long)b * p.sino_elems + ((long long)view * p.det.nv + v) * p.det.nu + u] = from_f32<T>(acc * p.dt);
+    return true;
+}
+
+__device__ __forceinline__ void fp_tma_init_bars(FpTmaShared &sh) {
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&sh.bar[0]), 1);
+        mbar_init(smem_u32(&sh.bar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+}
+
+// 128-byte aligned slab buffers at the start of the dynamic shared memory
+template <typename T>
+__device__ __forceinline__ void fp_tma_buffers(unsigned char *smem_raw, int buf_elems, int nbuf, T *&buf0, T *&buf1) {
+    const unsigned raw_u32 = smem_u32(smem_raw);
+    const unsigned pad = ((raw_u32 + 127u) & ~127u) - raw_u32;
+    buf0 = (T *)(smem_raw + pad);
+    buf1 = nbuf == 2 ? (T *)(smem_raw + pad + sizeof(T) * (size_t)buf_elems) : buf0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox cfg,
+                                                           const __grid_constant__ TmaMaps maps,
+                                                           const T *__restrict__ vol, T *__restrict__ sino) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ FpTmaShared sh;
+    T *buf0, *buf1;
+    fp_tma_buffers<T>(smem_raw, cfg.buf_elems, cfg.nbuf, buf0, buf1);
+    fp_tma_init_bars(sh);
+    unsigned ph[2] = {0u, 0u};
+    fp_tma_tile<T>(p, cfg, maps.map, vol, sino, blockIdx.z % p.n_views, blockIdx.z / p.n_views, blockIdx.x,
+                   blockIdx.y, buf0, buf1, sh, ph);
+}
+
+// Persistent launch over the (view, tile) items of several volumes: each CTA takes the next item
+// from a device counter until all are done. Volumes are ordered by decreasing cost per item.
+struct PlanMaps {
+    CUtensorMap map[PLAN_MAX][3];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TMA_NT, 2) fp_tma_batched_kernel(const __grid_constant__ PlanLaunch L,
+                                                                   const __grid_constant__ PlanMaps M) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ FpTmaShared sh;
+    __shared__ int s_item;
+    fp_tma_init_bars(sh);
+    unsigned ph[2] = {0u, 0u};
+    const long long total = L.item_end[L.n - 1];
+    for (;;) {
+        __syncthreads();   // every thread has read the previous item number
+        if (threadIdx.x == 0) s_item = atomicAdd(L.counter, 1);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int i = 0;
+        while (item >= L.item_end[i]) ++i;
+        const PlanVolume &V = L.v[i];
+        const long long local = item - (i ? L.item_end[i - 1] : 0);
+        const int tiles = V.ntx * V.nty;
+        const int view = (int)(local / tiles), t = (int)(local % tiles);
+        T *buf0, *buf1;
+        fp_tma_buffers<T>(smem_raw, V.cfg.buf_elems, V.cfg.nbuf, buf0, buf1);
+        if (!fp_tma_tile<T>(V.p, V.cfg, M.map[i], (const T *)V.in, (T *)V.out, view, 0, t % V.ntx, t / V.ntx, buf0,
+                            buf1, sh, ph))
+            return;
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -364,9 +447,9 @@ void tile_extents(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0, int 
                     mn1 = std::min(mn1, q1); mx1 = std::max(mx1, q1);
                     mn2 = std::min(mn2, q2); mx2 = std::max(mx2, q2);
                 }
-            // kernel: lo = floor(mn) - 1, hi = floor(mx) + 2 (clipped); extent <= ceil(mx - mn) + 4, +2 for FP32
-            double e1 = std::min(std::ceil(mx1 - mn1) + 6.0, (double)(dims[a1] + 2 * G + 2));
-            double e2 = std::min(std::ceil(mx2 - mn2) + 6.0, (double)(dims[a2] + 2 * G + 2));
+            // kernel: lo = floor(mn) - 1, hi = floor(mx) + 2 (clipped); extent <= ceil(mx - mn) + 4, +1 for FP32
+            double e1 = std::min(std::ceil(mx1 - mn1) + 5.0, (double)(dims[a1] + 2 * G + 2));
+            double e2 = std::min(std::ceil(mx2 - mn2) + 5.0, (double)(dims[a2] + 2 * G + 2));
             ext[m][a1] = std::max(ext[m][a1], e1);
             ext[m][a2] = std::max(ext[m][a2], e2);
         }
@@ -392,11 +475,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Box dimensions for the TMA kernel, or depth = 0 if it cannot be used (shared memory too small or
 // the row pitch is not a multiple of 16 bytes).
-FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem) {
+FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf) {
     FpTmaBox c{};
     const int align = 16 / (int)elem;
     if (((size_t)g->nx * elem) % 16 != 0) return c;
-    c.depth = 8;
+    // slab depth: a multiple of the x alignment so that x-march boxes start aligned
+    c.depth = depth > 0 ? ((depth + align - 1) / align) * align : 8;
+    c.nbuf = nbuf == 2 ? 2 : 1;   // default: one buffer (more CTAs per SM beat the copy overlap)
     double smin = std::min(g->sx, std::min(g->sy, g->sz));
     c.guard = 1 + (int)std::floor(g->dt / smin);
     // slab planes start so that (first plane - guard) is a multiple of the x alignment
@@ -438,7 +523,7 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem) {
         maxel = std::max(maxel, e[0] * e[1] * e[2]);
     }
     c.buf_elems = ((maxel * (int)elem + 127) / 128) * 128 / (int)elem;
-    if (2 * (size_t)c.buf_elems * elem > 200 * 1024) c.depth = 0;   // does not fit: use another kernel
+    if ((size_t)c.nbuf * c.buf_elems * elem > 200 * 1024) c.depth = 0;   // does not fit: use another kernel
     return c;
 }
 
@@ -449,7 +534,7 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
     const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
-    const size_t smem = 2 * sizeof(T) * (size_t)cfg.buf_elems + 128;
+    const size_t smem = (size_t)cfg.nbuf * sizeof(T) * (size_t)cfg.buf_elems + 128;
     cudaError_t e = cudaFuncSetAttribute(fp_tma_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     const int nx = p.vol.nx, ny = p.vol.ny, nz = p.vol.nz;
@@ -474,6 +559,80 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
         fp_tma_kernel<T><<<grid, TMA_NT, smem, st>>>(p, cfg, maps, vptr, (T *)sino + b0 * p.sino_elems);
     }
     return (int)cudaGetLastError();
+}
+
+template <typename T>
+static int encode_maps(const OpParams &p, const FpTmaBox &cfg, const void *vol, int nb, CUtensorMap maps[3]) {
+    auto enc = encode_fn();
+    if (!enc) return (int)cudaErrorNotSupported;
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    const int nx = p.vol.nx, ny = p.vol.ny, nz = p.vol.nz;
+    cuuint64_t gdim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nb};
+    cuuint64_t gstride[3] = {(cuuint64_t)nx * sizeof(T), (cuuint64_t)nx * ny * sizeof(T),
+                             (cuuint64_t)nx * ny * nz * sizeof(T)};
+    cuuint32_t estride[4] = {1, 1, 1, 1};
+    for (int m = 0; m < 3; ++m) {
+        cuuint32_t box[4] = {(cuuint32_t)cfg.bx[m], (cuuint32_t)cfg.by[m], (cuuint32_t)cfg.bz[m], 1};
+        CUresult r = enc(&maps[m], dt, 4, const_cast<void *>(vol), gdim, gstride, box, estride,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
+    }
+    return 0;
+}
+
+template <typename T>
+static int launch_batched_t(const PlanLaunch &L, int grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(fp_tma_batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    PlanMaps M;
+    std::memset(&M, 0, sizeof(M));
+    for (int i = 0; i < L.n; ++i) {
+        int rc = encode_maps<T>(L.v[i].p, L.v[i].cfg, L.v[i].in, 1, M.map[i]);
+        if (rc) return rc;
+    }
+    e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return (int)e;
+    fp_tma_batched_kernel<T><<<grid, TMA_NT, smem, st>>>(L, M);
+    return (int)cudaGetLastError();
+}
+
+int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_batched_t<float>(L, grid, smem, st);
+        case PYRONN_BF16: return launch_batched_t<__nv_bfloat16>(L, grid, smem, st);
+        case PYRONN_F16: return launch_batched_t<__half>(L, grid, smem, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int fp_tma_batched_occupancy(int dtype, size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaSuccess;
+    switch (dtype) {
+        case PYRONN_F32:
+            e = cudaFuncSetAttribute(fp_tma_batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fp_tma_batched_kernel<float>, TMA_NT, smem);
+            break;
+        case PYRONN_BF16:
+            e = cudaFuncSetAttribute(fp_tma_batched_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fp_tma_batched_kernel<__nv_bfloat16>,
+                                                                  TMA_NT, smem);
+            break;
+        case PYRONN_F16:
+            e = cudaFuncSetAttribute(fp_tma_batched_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fp_tma_batched_kernel<__half>, TMA_NT, smem);
+            break;
+        default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)e;
 }
 
 int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream) {

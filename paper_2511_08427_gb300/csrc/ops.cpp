@@ -79,7 +79,7 @@ const FpSlabCfg &fp_cfg(pyronn_geom_t g) {
 const FpTmaBox &tma_cfg(pyronn_geom_t g, int dtype) {
     std::lock_guard<std::mutex> lk(g->mu);
     if (!g->tma_ready[dtype]) {
-        g->tma_cfg[dtype] = choose_fp_tma_box(g, dtype_size(dtype));
+        g->tma_cfg[dtype] = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf);
         g->tma_ready[dtype] = 1;
     }
     return g->tma_cfg[dtype];
@@ -125,9 +125,29 @@ int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out) {
         out[6 + 3 * m] = tb.bz[m];
     }
     out[13] = tb.buf_elems;
-    out[14] = kernel == 3 ? (int)(2 * dtype_size(dtype) * (size_t)tb.buf_elems + 128)
+    out[14] = kernel == 3 ? (int)((size_t)tb.nbuf * dtype_size(dtype) * (size_t)tb.buf_elems + 128)
                           : (kernel == 2 ? (int)(sizeof(float) * (size_t)sc.smem_floats) : 0);
     out[15] = sc.smem_floats;
+    return PYRONN_OK;
+}
+
+int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
+    clear_error();
+    if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
+    std::lock_guard<std::mutex> lk(g->mu);
+    switch (param) {
+        case PYRONN_TUNE_FP_DEPTH:
+            if (value < 0 || value > 64) return set_error(PYRONN_INVALID_ARG, "slab depth %d out of [0, 64]", value);
+            g->tuning.fp_depth = value;
+            break;
+        case PYRONN_TUNE_FP_BUFFERS:
+            if (value < 0 || value > 2) return set_error(PYRONN_INVALID_ARG, "buffer count %d out of [0, 2]", value);
+            g->tuning.fp_nbuf = value;
+            break;
+        default:
+            return set_error(PYRONN_INVALID_ARG, "unknown tuning parameter %d", param);
+    }
+    g->tma_ready[0] = g->tma_ready[1] = g->tma_ready[2] = 0;
     return PYRONN_OK;
 }
 

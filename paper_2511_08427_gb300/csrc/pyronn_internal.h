@@ -85,6 +85,32 @@ struct FpTmaBox {
     int bx[3], by[3], bz[3];   // box extents (x, y, z) for march axis m = 0, 1, 2
     int depth, guard, slab0;   // slab depth (0: kernel unusable), guard planes, first slab plane
     int buf_elems;             // elements per buffer (max over axes)
+    int nbuf;                  // 1 or 2 shared-memory buffers
+};
+
+// Batched (persistent) launches: per-volume descriptions of one plan, in processing order.
+constexpr int PLAN_MAX = 16;
+struct PlanVolume {
+    OpParams p;                // batch = 1
+    FpTmaBox cfg;              // forward-projector boxes of this geometry and element type
+    const void *in;            // input buffer (volume for FP, sinogram for adjoint / BP)
+    void *out;                 // output buffer
+    int ntx, nty;              // work tiles: detector tiles (FP) or volume bricks in x, y (adjoint, BP)
+    int ntz;                   // bricks in z (adjoint, BP)
+    int per_item;              // views per item group: FP items are (view, tile)
+};
+struct PlanLaunch {
+    int n;
+    long long item_end[PLAN_MAX];   // cumulative item counts
+    PlanVolume v[PLAN_MAX];
+    int *counter;              // device work counter (zeroed before the launch)
+    int *flags;                // device flags (tensor-copy timeouts)
+};
+
+// Tuning knobs (pyronn_geom_set_tuning); 0 = automatic.
+struct Tuning {
+    int fp_depth = 0;          // slab depth of the TMA forward projector
+    int fp_nbuf = 0;           // its number of buffers
 };
 
 }  // namespace pyronn
@@ -124,6 +150,7 @@ struct pyronn_geom {
     pyronn::FpSlabCfg fp_cfg{};    // 0-initialised: chosen on first use
     int fp_cfg_ready = 0;
     pyronn::FpTmaBox tma_cfg[3] = {};   // per dtype
+    pyronn::Tuning tuning;
     int tma_ready[3] = {0, 0, 0};
     int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged (thread loads), 3 slab-staged (TMA)
     int adj_variant = 0;           // 0 auto, 1 atomic scatter, 2 output-stationary bricks
@@ -141,8 +168,14 @@ int finalize_geometry(pyronn_geom *g);          // build FP32 tables from views
 int ensure_device(pyronn_geom *g);               // upload tables to the current device
 OpParams make_params(const pyronn_geom *g, int batch);
 FpSlabCfg choose_fp_slab_cfg(const pyronn_geom *g);
-FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem);
+FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf);
 int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream);
+int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
+int launch_adjoint_brick_batched(const PlanLaunch &L, int dtype, int grid, void *stream);
+int adjoint_brick_batched_occupancy(int *blocks_per_sm);
+int launch_bp_brick_batched(const PlanLaunch &L, int dtype, int weight, int grid, void *stream);
+int bp_brick_batched_occupancy(int *blocks_per_sm);
+int fp_tma_batched_occupancy(int dtype, size_t smem, int *blocks_per_sm);
 
 // kernel launchers (return a cudaError_t as int)
 int launch_fp(const OpParams &p, const FpSlabCfg &cfg, const void *vol, void *sino, int dtype, void *stream);

@@ -171,6 +171,9 @@ class Geometry:
                 "box": [o[4:7], o[7:10], o[10:13]], "buf_elems": o[13], "smem_bytes": o[14],
                 "thread_box_capacity": o[15]}
 
+    def set_tuning(self, param: int, value: int) -> None:
+        check(lib().pyronn_geom_set_tuning(self._h, int(param), int(value)))
+
     def set_variant(self, op: int, variant: int) -> None:
         check(lib().pyronn_geom_set_variant(self._h, int(op), int(variant)))
 
@@ -266,6 +269,69 @@ def back_project_transpose(vol: torch.Tensor, g: Geometry, weight: int = BP_PLAI
         check(lib().pyronn_bp_transpose(g.handle, vol.data_ptr(), out.data_ptr(), dt, nb, int(weight),
                                         _stream_ptr(vol.device)))
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# batched plans
+# ------------------------------------------------------------------------------------------------
+
+class Plan:
+    """Several volumes with their own geometries, one persistent launch per operator.
+
+    Calls allocate nothing on the device (outputs passed in), so they can be captured in a CUDA graph
+    (torch.cuda.graph) after the plan has been created.
+    """
+
+    def __init__(self, geometries, dtype=torch.float32):
+        self.geometries = list(geometries)
+        self.dtype = dtype
+        arr = (ctypes.c_void_p * len(self.geometries))(*[g.handle.value if isinstance(g.handle, ctypes.c_void_p)
+                                                          else g.handle for g in self.geometries])
+        h = ctypes.c_void_p()
+        check(lib().pyronn_plan_create(len(self.geometries), arr, _DTYPES[dtype], ctypes.byref(h)))
+        self._h = h
+
+    def info(self) -> dict:
+        n = ctypes.c_int()
+        a = ctypes.c_int64()
+        b = ctypes.c_int64()
+        gr = (ctypes.c_int * 3)()
+        check(lib().pyronn_plan_info(self._h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(b), gr))
+        return {"n": n.value, "items_fp": a.value, "items_brick": b.value, "grids": list(gr)}
+
+    def _ptrs(self, tensors, shapes, what):
+        if len(tensors) != len(self.geometries):
+            raise ValueError(f"expected {len(self.geometries)} {what} tensors")
+        for t, shp in zip(tensors, shapes):
+            _check(t, what)
+            if t.dtype != self.dtype or tuple(t.shape) != tuple(shp) or not t.is_contiguous():
+                raise ValueError(f"{what}: expected contiguous {self.dtype} of shape {tuple(shp)}, got "
+                                 f"{t.dtype} {tuple(t.shape)}")
+        return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+    def forward_project(self, vols, sinos):
+        v = self._ptrs(vols, [g.volume_shape for g in self.geometries], "volume")
+        s = self._ptrs(sinos, [g.sinogram_shape for g in self.geometries], "sinogram")
+        check(lib().pyronn_plan_fp(self._h, v, s, _stream_ptr(vols[0].device)))
+        return sinos
+
+    def adjoint(self, sinos, vols):
+        s = self._ptrs(sinos, [g.sinogram_shape for g in self.geometries], "sinogram")
+        v = self._ptrs(vols, [g.volume_shape for g in self.geometries], "volume")
+        check(lib().pyronn_plan_adjoint(self._h, s, v, _stream_ptr(vols[0].device)))
+        return vols
+
+    def back_project(self, sinos, vols, weight: int = BP_PLAIN):
+        s = self._ptrs(sinos, [g.sinogram_shape for g in self.geometries], "sinogram")
+        v = self._ptrs(vols, [g.volume_shape for g in self.geometries], "volume")
+        check(lib().pyronn_plan_bp(self._h, s, v, int(weight), _stream_ptr(vols[0].device)))
+        return vols
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib._lib is not None:
+            _lib._lib.pyronn_plan_destroy(h)
+            self._h = None
 
 
 # ------------------------------------------------------------------------------------------------

@@ -322,11 +322,16 @@ def test_cone256_config_sampled(ops):
     vids = rng.choice(x.size, size=3000, replace=False)
     refb = oracle.bp_voxels(og, host(p), vids, 1)
     assert rel_l2(b.ravel()[vids], refb) <= 1e-5
-    # dot-product test at full size
-    yc = torch.randn(og.sino_shape, device=DEV)
+    # dot-product test at full size: non-negative cotangent (no cancellation, relative bound) and a
+    # signed one (bounded by the Cauchy-Schwarz scale of the inner products)
+    yc = torch.rand(og.sino_shape, device=DEV)
     lhs = float(np.vdot(host(p).ravel(), host(yc).ravel()))
     rhs = float(np.vdot(x.astype(np.float64).ravel(), host(ops.adjoint(yc, g)).ravel()))
     assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+    yc = torch.randn(og.sino_shape, device=DEV)
+    lhs = float(np.vdot(host(p).ravel(), host(yc).ravel()))
+    rhs = float(np.vdot(x.astype(np.float64).ravel(), host(ops.adjoint(yc, g)).ravel()))
+    assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(host(p)) * np.linalg.norm(host(yc))
 
 
 def test_variants_agree_at_full_size(ops):
