@@ -187,6 +187,77 @@ def run_reference(args):
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 
+def kernel_traffic(kernel: str, source: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, source), "rb") as f:
+            digest = hashlib.sha1(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    return rec.get("dram_bytes_per_launch") if rec.get("source_sha1") == digest else None
+
+
+def run_batched(dev, K: int = 3):
+    """16 volumes of uneven sizes (96^3 ... 256^3, circular / helical orbits, 180-540 views, 256^2-512^2
+    detectors) in one persistent launch per operator, FP32 and BF16 storage, plain and CUDA-graph replay."""
+    import torch
+    from paper_2511_08427_gb300 import inputs, operators as ops
+    specs = inputs.batched_cone_workload()
+    geoms, vols = [], []
+    for w in specs:
+        n = w["side"]
+        geoms.append(ops.Geometry.cone_circular((n, n, n), (w["voxel_mm"],) * 3, (w["det"], w["det"]),
+                                                (w["du"], w["du"]), w["views"], w["angular_range"], w["sid"],
+                                                w["sdd"], helical_pitch=w["pitch"]))
+        vols.append(inputs.rasterise_ellipsoids(inputs.random_ellipsoids(20, 0.5 * n * w["voxel_mm"], w["seed"]),
+                                                (n, n, n), (w["voxel_mm"],) * 3))
+    samples = sum(g.count_samples() for g in geoms)
+    out = {"workload": "16 cone-beam volumes 96^3..256^3, circular/helical, 180-540 views, 256^2-512^2 detectors",
+           "samples_per_fp": samples}
+    stream = torch.cuda.current_stream(dev)
+    for dtype, tag in ((torch.float32, "f32"), (torch.bfloat16, "bf16")):
+        plan = ops.Plan(geoms, dtype=dtype)
+        xs = [torch.from_numpy(v).to(dev).to(dtype) for v in vols]
+        sinos = [torch.empty(g.sinogram_shape, device=dev, dtype=dtype) for g in geoms]
+        adj = [torch.empty(g.volume_shape, device=dev, dtype=dtype) for g in geoms]
+        plan.forward_project(xs, sinos)
+        plan.adjoint(sinos, adj)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        for _ in range(K):
+            plan.forward_project(xs, sinos)
+        ev[1].record(stream)
+        for _ in range(K):
+            plan.adjoint(sinos, adj)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fp_ms = ev[0].elapsed_time(ev[1]) / K
+        adj_ms = ev[1].elapsed_time(ev[2]) / K
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                plan.forward_project(xs, sinos)
+                plan.adjoint(sinos, adj)
+        stream.wait_stream(side)
+        graph.replay()
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(K):
+            graph.replay()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        out[tag] = {"fp_ms": fp_ms, "adjoint_ms": adj_ms, "fp_gsamples_per_s": samples / (fp_ms * 1e-3) / 1e9,
+                    "graph_fwd_adj_ms": ev[0].elapsed_time(ev[1]) / K, "grids": plan.info()["grids"]}
+        del plan, xs, sinos, adj, graph
+    return out
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -203,6 +274,9 @@ def run_gpu(args):
 
     vol_np = build_inputs(seed_vol=3 + rank)
     g = make_geometry()
+    # slab depth / buffer count chosen by the project's autotuner (cached per device and geometry)
+    from paper_2511_08427_gb300 import autotune
+    tuned = autotune.tune_forward(g)
     n_samples = g.count_samples()
     n_updates = 256 ** 3 * 360
     vol = torch.from_numpy(vol_np).to(dev)
@@ -286,14 +360,7 @@ def run_gpu(args):
     achieved_tflops = n_samples * FP_FLOP_PER_SAMPLE / fp_mean_s / 1e12
     smem_peak_gbs = n_sm * 128 * sm_max * 1e6 / 1e9
     achieved_smem_gbs = n_samples * FP_SMEM_BYTES_PER_SAMPLE / fp_mean_s / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "fp_slab_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as f:
-                traffic = json.load(f).get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = kernel_traffic("fp_tma_kernel", "paper_2511_08427_gb300/csrc/k_fp_tma.cu")
 
     result = {
         "metric": METRIC, "value": fp_rate, "unit": "G ray-samples/s", "n_gpus": world, "steps": K,
@@ -310,7 +377,7 @@ def run_gpu(args):
         "gpu_launches": 3 * K,
         "clocks": clk,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / alu_peak_tflops, "traffic": traffic, "kernel": "fp_slab_kernel",
+                     "frac": achieved_tflops / alu_peak_tflops, "traffic": traffic, "kernel": "fp_tma_kernel",
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (unit counts, max clock)",
                      "flop_per_sample": FP_FLOP_PER_SAMPLE,
                      "smem": {"achieved_gbs": achieved_smem_gbs, "peak_gbs": smem_peak_gbs,
@@ -318,6 +385,9 @@ def run_gpu(args):
                               "bytes_per_sample": FP_SMEM_BYTES_PER_SAMPLE,
                               "peak_source": f"{n_sm} SMs x 128 B/clk x {sm_max:.0f} MHz"}},
     }
+    result["autotune"] = {k: tuned[k] for k in ("depth", "buffers", "ms", "cached")}
+    if not args.no_batched:
+        result["batched"] = run_batched(dev, K=max(3, args.steps // 2))
     if rank == 0 and not args.no_cpu_baseline:
         rate, s, dt, threads, nv = oracle_sample_rate(vol_np, 64, target_s=args.ref_seconds)
         result["cpu_baseline"] = {"value": rate, "unit": "G ray-samples/s", "cores": threads, "kind": "oracle",
@@ -338,6 +408,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -227,8 +227,10 @@ PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void 
  * shared-memory kernel filled by thread loads (falls back to 1 when the staged box cannot fit),
  * 3 slab-staged kernel filled by TMA tensor copies (needs a row pitch that is a multiple of 16
  * bytes; falls back to 2). op 1 = matched adjoint:
- * variant 0 automatic (= 2), 1 one-thread-per-ray FP32 global atomics, 2 output-stationary
- * bricks accumulated in shared memory. op 2 = voxel-driven back-projection: variant 0 automatic
+ * variant 0 automatic (= 3 where its box fits, else 2), 1 one-thread-per-ray FP32 global atomics,
+ * 2 output-stationary bricks accumulated in shared memory, 3 slab-ordered: detector tiles march
+ * the volume like the forward projector, scatter into shared-memory slab boxes and add each box to
+ * the volume with vector reductions. op 2 = voxel-driven back-projection: variant 0 automatic
  * (= 2), 1 one thread per voxel in absolute detector coordinates, 2 bricks with detector
  * coordinates relative to the brick centre's projection. All variants compute the same operator. */
 PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
@@ -259,6 +261,11 @@ PYRONN_API int pyronn_geom_read_flags(pyronn_geom_t g, int *out, int reset);
  * axes x, y, z, [13] elements per TMA buffer, [14] dynamic shared memory bytes per CTA,
  * [15] thread-staged box capacity (elements). */
 PYRONN_API int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out);
+
+/* Matched-adjoint configuration (host computation, no GPU needed), 4 ints: [0] kernel (1 atomic
+ * scatter, 2 bricks, 3 slab-ordered), [1] slab depth, [2] guard planes, [3] shared-memory box
+ * capacity in floats. */
+PYRONN_API int pyronn_geom_adjoint_config(pyronn_geom_t g, int *out);
 
 /* Message describing the last error of the calling thread ("" if none). */
 PYRONN_API const char *pyronn_last_error(void);

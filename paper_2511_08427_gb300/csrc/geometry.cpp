@@ -264,6 +264,8 @@ int finalize_geometry(pyronn_geom *g) {
     g->sample_count = -1;
     g->fp_cfg_ready = 0;
     g->tma_ready[0] = g->tma_ready[1] = g->tma_ready[2] = 0;
+    g->adj_cfg_ready = 0;
+    g->adj_cfg_ready = 0;
     return PYRONN_OK;
 }
 
@@ -527,6 +529,7 @@ int pyronn_geom_set_step(pyronn_geom_t g, double dt_mm) {
     g->sample_count = -1;
     g->fp_cfg_ready = 0;
     g->tma_ready[0] = g->tma_ready[1] = g->tma_ready[2] = 0;
+    g->adj_cfg_ready = 0;
     return PYRONN_OK;
 }
 

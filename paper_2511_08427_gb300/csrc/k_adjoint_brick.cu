@@ -48,8 +48,10 @@ __device__ __forceinline__ void floor_frac_clamped(float q, int &i, float &f) {
     f = q - (t - M);
 }
 
+// no "memory" clobber: the accumulator is read only after a barrier (a compiler fence), and a clobber
+// would make the compiler reload shared values after each reduction
 __device__ __forceinline__ void red_add_shared(unsigned addr, float v) {
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v));
 }
 
 // add the eight corner weights of cell (ix, iy, iz) to the brick accumulator (corners inside only)

@@ -1,0 +1,625 @@
+// Slab-ordered matched adjoint (same operator as adjoint_scatter_kernel, Sec. 2.2 A^T): the exact
+// transpose of the slab-staged forward projector's traversal.
+//
+// One CTA owns a 32 x 32 tile of detector pixels of one view (four rays per thread). It marches
+// through the volume in slabs along the tile's dominant axis m, exactly like the forward projector:
+// sample k of a ray belongs to slab s through integer boundaries computed by one FP32 formula, so
+// every sample is scattered once. For each slab the CTA zeroes a shared-memory box (the tile's
+// frustum in the slab, one voxel of margin), scatters y_r dt times the eight trilinear weights of
+// every sample into it (weights accumulated in registers while a ray stays in one cell, flushed with
+// shared-memory reductions), and then adds the box to the output volume with float4 global
+// reductions, skipping all-zero groups.
+//
+// Precision: as in the brick adjoint, sample positions are formed relative to an anchor, here the
+// centre X_s of each slab's box, from FP64 per-(tile, slab) constants (one lane per slab): the point
+// where the tile's corner ray meets the plane through X_s, the per-pixel steps of that point, and
+// the lattice phase of the corner ray at X_s. Each ray then needs only small FP32 quantities.
+//
+// Lanes of a warp take rays 4 pixels apart in u and 8 in v, so their samples rarely share a voxel.
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "device_common.cuh"
+#include "host_rays.h"
+
+namespace pyronn {
+
+constexpr int AS_TU = 32, AS_TV = 32, AS_NT = 256, AS_RPT = 4;
+constexpr int AS_MAX_SLABS = 80;
+
+struct AsTile {                 // per tile (FP64-derived)
+    float D[3], Cu[3], Cv[3];   // corner-ray direction and its per-pixel steps
+    float inv_nD, nD2;
+    float dref[3];
+};
+
+struct AsSlab {                 // per (tile, slab), relative to the box centre X_s
+    float A[3], Eu[3], Ev[3];   // corner-ray point on the plane through X_s, per-pixel steps
+    float Xs[3];                // X_s - C (world mm)
+    float o[3];                 // box-local index of X_s
+    float f;                    // phase of the corner ray at X_s: (X_s - C) . dref = (K + f) dt
+    int lo[3], ext[3];          // box origin and extents (voxels); ext[0] == 0: empty slab
+};
+
+struct AsShared {
+    float corner[5][6];
+    AsTile tile;
+    AsSlab slab[AS_MAX_SLABS];
+    int srange[2];
+};
+
+__device__ __forceinline__ void as_floor_frac(float q, int &i, float &f) {
+    const float M = 12582912.0f;
+    q = fminf(fmaxf(q, -1.0e6f), 1.0e6f);
+    const float t = __fadd_rd(q, M);
+    i = __float_as_int(t) - 0x4B400000;
+    f = q - (t - M);
+}
+
+// no "memory" clobber: the box is read only after a barrier (a compiler fence), and a clobber would
+// make the compiler reload every shared value after each reduction
+__device__ __forceinline__ void as_red_shared(unsigned addr, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v));
+}
+
+// FP64 constants of slab s (box lo / ext already set): plane through the box centre.
+__device__ void as_slab_setup(const OpParams &p, int view, int u0, int v0, AsSlab &S) {
+    const double *x = p.views64 + (size_t)view * VIEW64_STRIDE;
+    const double sp[3] = {p.sx, p.sy, p.sz};
+    const double hv3[3] = {0.5 * (p.vol.nx - 1), 0.5 * (p.vol.ny - 1), 0.5 * (p.vol.nz - 1)};
+    double Xb[3];
+    for (int a = 0; a < 3; ++a) {
+        const double ci = S.lo[a] + 0.5 * (S.ext[a] - 1);   // box centre, volume index
+        Xb[a] = (ci - hv3[a]) * sp[a];
+        S.o[a] = (float)(0.5 * (S.ext[a] - 1));
+        S.Xs[a] = (float)Xb[a];
+    }
+    double A[3], Eu[3], Ev[3], D[3];
+    if (p.perspective) {
+        const double *Sx = x + 12, *c0 = x + 15, *c1 = x + 18, *c2 = x + 21, *nrm = x + 24;
+        const double lam = ((Xb[0] - Sx[0]) * nrm[0] + (Xb[1] - Sx[1]) * nrm[1] + (Xb[2] - Sx[2]) * nrm[2]) / x[27];
+        for (int i = 0; i < 3; ++i) {
+            D[i] = c2[i] + u0 * c0[i] + v0 * c1[i];
+            A[i] = Sx[i] + lam * D[i] - Xb[i];
+            Eu[i] = lam * c0[i];
+            Ev[i] = lam * c1[i];
+        }
+    } else {
+        const double *Dc = x, *eu = x + 3, *ev = x + 6, *d = x + 9;
+        const double hu = 0.5 * (p.det.nu - 1), hvv = 0.5 * (p.det.nv - 1);
+        const double su = (u0 - hu) * p.du + p.ou, sv = (v0 - hvv) * p.dv + p.ov;
+        double a0[3], du_[3], dv_[3];
+        for (int i = 0; i < 3; ++i) {
+            a0[i] = Dc[i] + su * eu[i] + sv * ev[i] - Xb[i];
+            du_[i] = p.du * eu[i];
+            dv_[i] = p.dv * ev[i];
+            D[i] = d[i];
+        }
+        const double pa = a0[0] * d[0] + a0[1] * d[1] + a0[2] * d[2];
+        const double pu = du_[0] * d[0] + du_[1] * d[1] + du_[2] * d[2];
+        const double pv = dv_[0] * d[0] + dv_[1] * d[1] + dv_[2] * d[2];
+        for (int i = 0; i < 3; ++i) {
+            A[i] = a0[i] - pa * d[i];
+            Eu[i] = du_[i] - pu * d[i];
+            Ev[i] = dv_[i] - pv * d[i];
+        }
+    }
+    const double nD = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    const double T = (Xb[0] * D[0] + Xb[1] * D[1] + Xb[2] * D[2]) / nD / (double)p.dt;
+    for (int i = 0; i < 3; ++i) {
+        S.A[i] = (float)A[i];
+        S.Eu[i] = (float)Eu[i];
+        S.Ev[i] = (float)Ev[i];
+    }
+    S.f = (float)(T - floor(T));
+}
+
+__device__ void as_tile_setup(const OpParams &p, int view, int u0, int v0, AsTile &t) {
+    const double *x = p.views64 + (size_t)view * VIEW64_STRIDE;
+    double D[3], Cu[3], Cv[3];
+    if (p.perspective) {
+        const double *c0 = x + 15, *c1 = x + 18, *c2 = x + 21;
+        for (int i = 0; i < 3; ++i) {
+            D[i] = c2[i] + u0 * c0[i] + v0 * c1[i];
+            Cu[i] = c0[i];
+            Cv[i] = c1[i];
+        }
+    } else {
+        for (int i = 0; i < 3; ++i) {
+            D[i] = x[9 + i];
+            Cu[i] = 0.0;
+            Cv[i] = 0.0;
+        }
+    }
+    const double nD2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+    const double nD = sqrt(nD2);
+    for (int i = 0; i < 3; ++i) {
+        t.D[i] = (float)D[i];
+        t.Cu[i] = (float)Cu[i];
+        t.Cv[i] = (float)Cv[i];
+        t.dref[i] = (float)(D[i] / nD);
+    }
+    t.inv_nD = (float)(1.0 / nD);
+    t.nD2 = (float)nD2;
+}
+
+// Ray (u0 + du, v0 + dv) of the tile: unit direction d and its change from the corner ray dd
+// (formed without cancellation, as in the brick adjoint).
+__device__ __forceinline__ void as_ray_dir(const AsTile &T, float fu, float fv, float d[3], float dd[3]) {
+    const float L0 = fmaf(fv, T.Cv[0], fu * T.Cu[0]);
+    const float L1 = fmaf(fv, T.Cv[1], fu * T.Cu[1]);
+    const float L2 = fmaf(fv, T.Cv[2], fu * T.Cu[2]);
+    const float DL = fmaf(T.D[0], L0, fmaf(T.D[1], L1, T.D[2] * L2));
+    const float LL = fmaf(L0, L0, fmaf(L1, L1, L2 * L2));
+    const float eps = (2.0f * DL + LL) / T.nD2;
+    const float sq = sqrtf(1.0f + eps);
+    const float inv = T.inv_nD / sq;
+    d[0] = (T.D[0] + L0) * inv;
+    d[1] = (T.D[1] + L1) * inv;
+    d[2] = (T.D[2] + L2) * inv;
+    const float g = -eps / (sq * (1.0f + sq));
+    dd[0] = fmaf(T.dref[0], g, L0 * inv);
+    dd[1] = fmaf(T.dref[1], g, L1 * inv);
+    dd[2] = fmaf(T.dref[2], g, L2 * inv);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int depth, int guard, int box_cap,
+                                                                const T *__restrict__ sino, float *__restrict__ vol) {
+    extern __shared__ __align__(16) float box[];
+    __shared__ AsShared sh;
+    const int view = blockIdx.z % p.n_views;
+    const int b = blockIdx.z / p.n_views;
+    const int tu0 = blockIdx.x * AS_TU, tv0 = blockIdx.y * AS_TV;
+    const int tu1 = min(tu0 + AS_TU, p.det.nu) - 1, tv1 = min(tv0 + AS_TV, p.det.nv) - 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const T *sb = sino + (long long)b * p.sino_elems + (long long)view * p.det.nv * p.det.nu;
+    float *vb = vol + (long long)b * p.vol_elems;
+    const FpRec &rec = p.fp[view];
+    const float dt = p.dt;
+
+    // corner and centre rays (FP32, global index coordinates) for the slab boxes
+    if (tid < 5) {
+        float cu, cv;
+        if (tid < 4) {
+            cu = (float)((tid & 1) ? tu1 : tu0);
+            cv = (float)((tid & 2) ? tv1 : tv0);
+        } else {
+            cu = 0.5f * (float)(tu0 + tu1);
+            cv = 0.5f * (float)(tv0 + tv1);
+        }
+        RayIdx c = ray_setup(rec, p.vol, cu, cv);
+        sh.corner[tid][0] = c.cx; sh.corner[tid][1] = c.cy; sh.corner[tid][2] = c.cz;
+        sh.corner[tid][3] = c.dx; sh.corner[tid][4] = c.dy; sh.corner[tid][5] = c.dz;
+    }
+    if (tid == 32) as_tile_setup(p, view, tu0, tv0, sh.tile);
+    if (tid == 64) {
+        sh.srange[0] = 1 << 30;
+        sh.srange[1] = -(1 << 30);
+    }
+    __syncthreads();
+
+    int m;
+    {
+        const float ax = fabsf(sh.corner[4][3]), ay = fabsf(sh.corner[4][4]), az = fabsf(sh.corner[4][5]);
+        m = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    }
+    const int a1 = (m == 0) ? 1 : 0, a2 = (m == 2) ? 1 : 2;
+    const int dims[3] = {p.vol.nx, p.vol.ny, p.vol.nz};
+    const int Nm = dims[m];
+    const int D = depth, G = guard;
+    const int base0 = -1;
+    const int nslab_all = (Nm + 1 - base0 + D - 1) / D;
+
+    // rays of this thread: lanes 4 pixels apart in u, 8 in v
+    int ru[AS_RPT], rv[AS_RPT];
+#pragma unroll
+    for (int j = 0; j < AS_RPT; ++j) {
+        ru[j] = tu0 + (lane & 7) * 4 + (warp & 3);
+        rv[j] = tv0 + (lane >> 3) * 8 + (warp >> 2) * 4 + j;
+    }
+    // slab range of the tile from the rays' in-box sample ranges
+#pragma unroll
+    for (int j = 0; j < AS_RPT; ++j) {
+        if (ru[j] > tu1 || rv[j] > tv1) continue;
+        RayIdx r = ray_setup(rec, p.vol, (float)ru[j], (float)rv[j]);
+        int k0, k1;
+        if (!ray_k_range(r, p.vol, dt, k0, k1)) continue;
+        const float cm = m == 0 ? r.cx : (m == 1 ? r.cy : r.cz);
+        const float dm = m == 0 ? r.dx : (m == 1 ? r.dy : r.dz);
+        const float qa = fmaf(fmaf((float)k0, dt, 0.5f * dt), dm, cm);
+        const float qb = fmaf(fmaf((float)k1, dt, 0.5f * dt), dm, cm);
+        const float qlo = fmaxf(fminf(qa, qb), -1.0f), qhi = fminf(fmaxf(qa, qb), (float)Nm);
+        int slo = ((int)floorf(qlo) - base0) / D, shi = ((int)floorf(qhi) - base0) / D;
+        slo = max(min(slo, nslab_all - 1), 0);
+        shi = max(min(shi, nslab_all - 1), 0);
+        atomicMin(&sh.srange[0], slo);
+        atomicMax(&sh.srange[1], shi);
+    }
+    __syncthreads();
+    const int s_first = sh.srange[0];
+    const int nsl = sh.srange[1] >= s_first ? min(sh.srange[1] - s_first + 1, AS_MAX_SLABS) : 0;
+    if (nsl <= 0) return;
+
+    // slab boxes (FP32 from the corner rays, as in the forward projector) and FP64 anchors, one lane per slab
+    for (int i = tid; i < nsl; i += AS_NT) {
+        AsSlab &S = sh.slab[i];
+        const int s = s_first + i;
+        const int b_lo = base0 + s * D;
+        const int b_hi = min(b_lo + D, Nm);
+        int lo[3], hi[3];
+        lo[m] = max(b_lo - G, -1 - G);
+        hi[m] = min(b_hi + G, Nm + G);
+        float mn1 = 3e38f, mx1 = -3e38f, mn2 = 3e38f, mx2 = -3e38f;
+        const float planes[2] = {(float)(b_lo - G), (float)(b_hi + G)};
+        for (int c = 0; c < 4; ++c) {
+            const float *cr = sh.corner[c];
+            const float idm = 1.0f / cr[3 + m];
+            for (int pl = 0; pl < 2; ++pl) {
+                const float t = (planes[pl] - cr[m]) * idm;
+                const float q1 = fmaf(t, cr[3 + a1], cr[a1]);
+                const float q2 = fmaf(t, cr[3 + a2], cr[a2]);
+                mn1 = fminf(mn1, q1); mx1 = fmaxf(mx1, q1);
+                mn2 = fminf(mn2, q2); mx2 = fmaxf(mx2, q2);
+            }
+        }
+        const float gf = (float)(G + 2);
+        mn1 = fmaxf(mn1, -gf); mx1 = fminf(mx1, (float)dims[a1] + gf);
+        mn2 = fmaxf(mn2, -gf); mx2 = fminf(mx2, (float)dims[a2] + gf);
+        lo[a1] = max((int)floorf(mn1) - 1, -1 - G);
+        hi[a1] = min((int)floorf(mx1) + 2, dims[a1] + G);
+        lo[a2] = max((int)floorf(mn2) - 1, -1 - G);
+        hi[a2] = min((int)floorf(mx2) + 2, dims[a2] + G);
+        // x origin on a 4-voxel boundary (float4 reductions into the volume)
+        lo[0] = lo[0] >= 0 ? (lo[0] & ~3) : -(((-lo[0]) + 3) & ~3);
+        int e0 = hi[0] - lo[0] + 1;
+        e0 = (e0 + 3) & ~3;
+        const int e1 = hi[1] - lo[1] + 1, e2 = hi[2] - lo[2] + 1;
+        const bool fits = e0 > 0 && e1 > 0 && e2 > 0 && (long long)e0 * e1 * e2 <= box_cap;
+        for (int a = 0; a < 3; ++a) S.lo[a] = lo[a];
+        S.ext[0] = fits ? e0 : 0;
+        S.ext[1] = e1;
+        S.ext[2] = e2;
+        if (fits) as_slab_setup(p, view, tu0, tv0, S);
+    }
+    __syncthreads();
+
+    const unsigned box_base = (unsigned)__cvta_generic_to_shared(box);
+    const float isx = p.vol.isx, isy = p.vol.isy, isz = p.vol.isz;
+    const bool vec4 = (p.vol.nx & 3) == 0;
+
+    for (int i = 0; i < nsl; ++i) {
+        const AsSlab &S = sh.slab[i];
+        const int s = s_first + i;
+        if (S.ext[0] == 0) {
+            // the tile's footprint in this slab does not fit the box: never expected (the host bound
+            // covers every tile); counted, and the slab's samples go straight to global atomics
+            if (tid == 0) atomicAdd(p.flags + FLAG_SLAB_OVERFLOW, 1);
+        }
+        const int Ex = S.ext[0], Ey = S.ext[1], Ez = S.ext[2];
+        const int lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2];
+        const unsigned sy4 = 4u * (unsigned)Ex, sz4 = 4u * (unsigned)(Ex * Ey);
+        const int nbox = Ex * Ey * Ez;
+        for (int e = tid; e < nbox; e += AS_NT) box[e] = 0.0f;
+        __syncthreads();
+        const int b_lo = base0 + s * D;
+        const int b_hi = min(b_lo + D, Nm);
+#pragma unroll 1
+        for (int j = 0; j < AS_RPT; ++j) {
+            const int u = ru[j], v = rv[j];
+            if (u > tu1 || v > tv1) continue;
+            float y = ldg_f32(sb + (long long)v * p.det.nu + u);
+            if (y == 0.0f) continue;
+            y *= dt;
+            // slab partition on the global FP32 ray (identical formula for the shared boundaries)
+            const RayIdx r = ray_setup(rec, p.vol, (float)u, (float)v);
+            int k0, k1;
+            if (!ray_k_range(r, p.vol, dt, k0, k1)) continue;
+            const float cm = m == 0 ? r.cx : (m == 1 ? r.cy : r.cz);
+            const float dm = m == 0 ? r.dx : (m == 1 ? r.dy : r.dz);
+            if (!(fabsf(dm) > 1e-3f * (fabsf(r.dx) + fabsf(r.dy) + fabsf(r.dz)))) {
+                // a ray barely advancing along m: scattered directly by the first slab
+                if (i == 0) {
+                    atomicAdd(p.flags + FLAG_SLAB_DIRECT_RAY, 1);
+                    for (int k = k0; k <= k1; ++k) {
+                        const float t = fmaf((float)k, dt, 0.5f * dt);
+                        const float qx = fmaf(t, r.dx, r.cx), qy = fmaf(t, r.dy, r.cy), qz = fmaf(t, r.dz, r.cz);
+                        const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+                        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+                        const float ax = qx - fx, ay = qy - fy, az = qz - fz;
+                        for (int c = 0; c < 8; ++c) {
+                            const int cx = ix + (c & 1), cy = iy + ((c >> 1) & 1), cz = iz + (c >> 2);
+                            if ((unsigned)cx < (unsigned)p.vol.nx && (unsigned)cy < (unsigned)p.vol.ny &&
+                                (unsigned)cz < (unsigned)p.vol.nz) {
+                                const float w = ((c & 1) ? ax : 1.0f - ax) * (((c >> 1) & 1) ? ay : 1.0f - ay) *
+                                                ((c >> 2) ? az : 1.0f - az);
+                                atomicAdd(vb + ((long long)cz * p.vol.ny + cy) * p.vol.nx + cx, y * w);
+                            }
+                        }
+                    }
+                }
+                continue;
+            }
+            const float inv_step = 1.0f / (dt * dm);
+            int ka, kb;
+            if (dm > 0.0f) {
+                ka = (int)ceilf(fmaf((float)b_lo - cm, inv_step, -0.5f));
+                kb = (int)ceilf(fmaf((float)b_hi - cm, inv_step, -0.5f)) - 1;
+            } else {
+                ka = (int)floorf(fmaf((float)b_hi - cm, inv_step, -0.5f)) + 1;
+                kb = (int)floorf(fmaf((float)b_lo - cm, inv_step, -0.5f));
+            }
+            ka = max(ka, k0);
+            kb = min(kb, k1);
+            if (ka > kb) continue;
+            if (Ex == 0) {
+                for (int k = ka; k <= kb; ++k) {
+                    const float t = fmaf((float)k, dt, 0.5f * dt);
+                    const float qx = fmaf(t, r.dx, r.cx), qy = fmaf(t, r.dy, r.cy), qz = fmaf(t, r.dz, r.cz);
+                    const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+                    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+                    const float ax = qx - fx, ay = qy - fy, az = qz - fz;
+                    for (int c = 0; c < 8; ++c) {
+                        const int cx = ix + (c & 1), cy = iy + ((c >> 1) & 1), cz = iz + (c >> 2);
+                        if ((unsigned)cx < (unsigned)p.vol.nx && (unsigned)cy < (unsigned)p.vol.ny &&
+                            (unsigned)cz < (unsigned)p.vol.nz) {
+                            const float w = ((c & 1) ? ax : 1.0f - ax) * (((c >> 1) & 1) ? ay : 1.0f - ay) *
+                                            ((c >> 2) ? az : 1.0f - az);
+                            atomicAdd(vb + ((long long)cz * p.vol.ny + cy) * p.vol.nx + cx, y * w);
+                        }
+                    }
+                }
+                continue;
+            }
+            // precise local ray: point on the plane through X_s, unit direction, phase
+            const float fu = (float)(u - tu0), fv = (float)(v - tv0);
+            float d[3], dd[3];
+            as_ray_dir(sh.tile, fu, fv, d, dd);
+            const float P0 = fmaf(fv, S.Ev[0], fmaf(fu, S.Eu[0], S.A[0]));
+            const float P1 = fmaf(fv, S.Ev[1], fmaf(fu, S.Eu[1], S.A[1]));
+            const float P2 = fmaf(fv, S.Ev[2], fmaf(fu, S.Eu[2], S.A[2]));
+            const float e = fmaf(S.Xs[0], dd[0], fmaf(S.Xs[1], dd[1], S.Xs[2] * dd[2])) +
+                            fmaf(P0, d[0], fmaf(P1, d[1], P2 * d[2]));
+            // sample k sits at s = (k - K + 1/2 - f) dt - e along d from P, K = floor of the phase:
+            // the integer part is recovered from the global ray's position of sample ka
+            const float tka = fmaf((float)ka, dt, 0.5f * dt);
+            // global FP32 estimate of s for sample ka, rounded to the lattice of the local phase
+            const float qcx = fmaf(tka, r.dx, r.cx), qcy = fmaf(tka, r.dy, r.cy), qcz = fmaf(tka, r.dz, r.cz);
+            // s of sample ka: projection onto d of (X_ka - (X_s + P)) in world mm
+            const float hx = 0.5f * (p.vol.nx - 1), hy = 0.5f * (p.vol.ny - 1), hz = 0.5f * (p.vol.nz - 1);
+            const float wx = (qcx - hx) / isx - (S.Xs[0] + P0);
+            const float wy = (qcy - hy) / isy - (S.Xs[1] + P1);
+            const float wz = (qcz - hz) / isz - (S.Xs[2] + P2);
+            const float s_est = fmaf(wx, d[0], fmaf(wy, d[1], wz * d[2]));
+            const float jf = rintf((s_est + e) / dt - 0.5f + S.f);   // k - K for sample ka
+            const float c_r = (0.5f - S.f) * dt - e;
+            const float qP0 = fmaf(P0, isx, S.o[0]), qP1 = fmaf(P1, isy, S.o[1]), qP2 = fmaf(P2, isz, S.o[2]);
+            const float qd0 = d[0] * isx, qd1 = d[1] * isy, qd2 = d[2] * isz;
+            float a0 = 0.f, a1v = 0.f, a2v = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f, a7 = 0.f;
+            int pix = 0, piy = 0, piz = 0, pkey = -1;
+            float jj = jf;
+            for (int k = ka; k <= kb + 1; ++k, jj += 1.0f) {
+                int key = -2, ix = 0, iy = 0, iz = 0;
+                float ax = 0.f, ay = 0.f, az = 0.f;
+                if (k <= kb) {
+                    const float sj = fmaf(jj, dt, c_r);
+                    as_floor_frac(fmaf(sj, qd0, qP0), ix, ax);
+                    as_floor_frac(fmaf(sj, qd1, qP1), iy, ay);
+                    as_floor_frac(fmaf(sj, qd2, qP2), iz, az);
+                    key = ((iz + 16) << 20) | ((iy + 16) << 10) | (ix + 16);
+                }
+                if (key != pkey) {
+                    if (pkey >= 0) {
+                        if ((unsigned)pix < (unsigned)(Ex - 1) && (unsigned)piy < (unsigned)(Ey - 1) &&
+                            (unsigned)piz < (unsigned)(Ez - 1)) {
+                            // the cell's 2 x 2 x 2 block lies in the box: eight reductions (corners outside the
+                            // volume land in the box margin and are dropped when the box is added)
+                            const unsigned a = box_base + 4u * (unsigned)((piz * Ey + piy) * Ex + pix);
+                            as_red_shared(a, a0);
+                            as_red_shared(a + 4u, a1v);
+                            as_red_shared(a + sy4, a2v);
+                            as_red_shared(a + sy4 + 4u, a3);
+                            as_red_shared(a + sz4, a4);
+                            as_red_shared(a + sz4 + 4u, a5);
+                            as_red_shared(a + sz4 + sy4, a6);
+                            as_red_shared(a + sz4 + sy4 + 4u, a7);
+                        } else {
+                            // outside the box: never expected (the box covers the tile's frustum); corners
+                            // inside the volume go to global memory and are counted
+                            const float vals[8] = {a0, a1v, a2v, a3, a4, a5, a6, a7};
+                            for (int c = 0; c < 8; ++c) {
+                                const int gx = pix + (c & 1) + lo0, gy = piy + ((c >> 1) & 1) + lo1,
+                                          gz = piz + (c >> 2) + lo2;
+                                if ((unsigned)gx < (unsigned)p.vol.nx && (unsigned)gy < (unsigned)p.vol.ny &&
+                                    (unsigned)gz < (unsigned)p.vol.nz) {
+                                    atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
+                                    atomicAdd(vb + ((long long)gz * p.vol.ny + gy) * p.vol.nx + gx, vals[c]);
+                                }
+                            }
+                        }
+                    }
+                    a0 = a1v = a2v = a3 = a4 = a5 = a6 = a7 = 0.f;
+                    pkey = key;
+                    pix = ix; piy = iy; piz = iz;
+                }
+                if (k <= kb) {
+                    const float wz1 = y * az, wz0 = y - wz1;
+                    const float w00 = wz0 * (1.f - ay), w01 = wz0 * ay, w10 = wz1 * (1.f - ay), w11 = wz1 * ay;
+                    a0 = fmaf(w00, 1.f - ax, a0);
+                    a1v = fmaf(w00, ax, a1v);
+                    a2v = fmaf(w01, 1.f - ax, a2v);
+                    a3 = fmaf(w01, ax, a3);
+                    a4 = fmaf(w10, 1.f - ax, a4);
+                    a5 = fmaf(w10, ax, a5);
+                    a6 = fmaf(w11, 1.f - ax, a6);
+                    a7 = fmaf(w11, ax, a7);
+                }
+            }
+        }
+        __syncthreads();
+        // add the box to the volume: float4 groups along x, all-zero groups skipped
+        if (Ex > 0) {
+            const int gx4 = Ex >> 2;
+            const int ngroups = gx4 * Ey * Ez;
+            for (int gi = tid; gi < ngroups; gi += AS_NT) {
+                const int xg = gi % gx4, row = gi / gx4;
+                const int ly = row % Ey, lz = row / Ey;
+                const float4 q = *reinterpret_cast<const float4 *>(box + (row * Ex + 4 * xg));
+                if (q.x == 0.f && q.y == 0.f && q.z == 0.f && q.w == 0.f) continue;
+                const int gx = lo0 + 4 * xg, gy = lo1 + ly, gz = lo2 + lz;
+                if ((unsigned)gy >= (unsigned)p.vol.ny || (unsigned)gz >= (unsigned)p.vol.nz) continue;
+                float *dst = vb + ((long long)gz * p.vol.ny + gy) * p.vol.nx + gx;
+                if (vec4 && gx >= 0 && gx + 3 < p.vol.nx) {
+                    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(q.x), "f"(q.y),
+                                 "f"(q.z), "f"(q.w)
+                                 : "memory");
+                } else {
+                    const float vv[4] = {q.x, q.y, q.z, q.w};
+                    for (int c = 0; c < 4; ++c)
+                        if ((unsigned)(gx + c) < (unsigned)p.vol.nx && vv[c] != 0.f) atomicAdd(dst + c, vv[c]);
+                }
+            }
+        }
+        __syncthreads();   // the box is reused by the next slab
+    }
+}
+
+template <typename T>
+__global__ void adjoint_convert_kernel(const float *__restrict__ src, T *__restrict__ dst, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) dst[i] = from_f32<T>(src[i]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// Largest box (floats) of one 32 x 32 tile over its first and last slab (the box extent is convex in
+// the slab position). Margins follow the kernel: lo = floor(min) - 1, hi = floor(max) + 2, x start
+// rounded down to 4 and x extent up to 4, +1 for FP32 rounding.
+long long as_tile_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0, int D, int G) {
+    const int tu1 = std::min(tu0 + AS_TU, g->nu) - 1, tv1 = std::min(tv0 + AS_TV, g->nv) - 1;
+    RayD cr[4];
+    for (int c = 0; c < 4; ++c) cr[c] = ray_setup_d(rec, g, (c & 1) ? tu1 : tu0, (c & 2) ? tv1 : tv0);
+    const RayD ctr = ray_setup_d(rec, g, 0.5 * (tu0 + tu1), 0.5 * (tv0 + tv1));
+    const int dims[3] = {g->nx, g->ny, g->nz};
+    const double amax = std::max(std::fabs(ctr.d[0]), std::max(std::fabs(ctr.d[1]), std::fabs(ctr.d[2])));
+    long long best = 0;
+    for (int m = 0; m < 3; ++m) {
+        if (std::fabs(ctr.d[m]) < 0.999 * amax) continue;
+        const int a1 = (m == 0) ? 1 : 0, a2 = (m == 2) ? 1 : 2;
+        const int Nm = dims[m];
+        const int nslab = (Nm + 2 + D - 1) / D;
+        for (int which = 0; which < 2; ++which) {
+            const int s = which ? nslab - 1 : 0;
+            const int b_lo = -1 + s * D, b_hi = std::min(b_lo + D, Nm);
+            const double planes[2] = {(double)(b_lo - G), (double)(b_hi + G)};
+            double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+            for (int c = 0; c < 4; ++c)
+                for (int pl = 0; pl < 2; ++pl) {
+                    const double t = (planes[pl] - cr[c].c[m]) / cr[c].d[m];
+                    for (int a : {a1, a2}) {
+                        const double q = cr[c].c[a] + t * cr[c].d[a];
+                        mn[a] = std::min(mn[a], q);
+                        mx[a] = std::max(mx[a], q);
+                    }
+                }
+            long long e[3];
+            for (int a = 0; a < 3; ++a) {
+                if (a == m) e[a] = D + 2 * G + 1;
+                else e[a] = (long long)std::ceil(mx[a] - mn[a]) + 5;
+                e[a] = std::min<long long>(e[a], dims[a] + 2 * G + 2);
+            }
+            e[0] = ((e[0] + 3 + 3) / 4) * 4;   // x start rounded down (<= 3 more), extent rounded up
+            best = std::max(best, e[0] * e[1] * e[2]);
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+static long long as_bound(const pyronn_geom *g, int depth, int guard) {
+    const int ntu = (g->nu + AS_TU - 1) / AS_TU, ntv = (g->nv + AS_TV - 1) / AS_TV;
+    std::atomic<int> next(0);
+    std::atomic<long long> best(0);
+    auto work = [&]() {
+        long long local = 0;
+        for (int n = next.fetch_add(1); n < g->n_views; n = next.fetch_add(1))
+            for (int j = 0; j < ntv; ++j)
+                for (int i = 0; i < ntu; ++i)
+                    local = std::max(local, as_tile_bound(g, g->fp_rec[n], i * AS_TU, j * AS_TV, depth, guard));
+        long long cur = best.load();
+        while (local > cur && !best.compare_exchange_weak(cur, local)) {
+        }
+    };
+    const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned i = 1; i < nt; ++i) th.emplace_back(work);
+    work();
+    for (auto &t : th) t.join();
+    return best.load();
+}
+
+// Deepest slab (8, 6 or 4 planes, and at most AS_MAX_SLABS slabs per tile) whose box fits in ~100 KB,
+// so that two CTAs share an SM; otherwise the shallowest that fits in 160 KB.
+AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
+    AdjSlabCfg c{};
+    if (g->ndim != 3) return c;
+    const int nmax = std::max(g->nx, std::max(g->ny, g->nz));
+    const int dmin = (nmax + 2 + AS_MAX_SLABS - 1) / AS_MAX_SLABS;
+    const double smin = std::min(g->sx, std::min(g->sy, g->sz));
+    c.guard = 1 + (int)std::floor(g->dt / smin);
+    const long long soft = (100 * 1024) / 4, hard = (160 * 1024) / 4;
+    long long need = 0;
+    for (int d : {8, 6, 4}) {
+        const int depth = std::max(d, dmin);
+        need = as_bound(g, depth, c.guard);
+        c.depth = depth;
+        if (need <= soft) break;
+    }
+    c.box_cap = (int)std::min(need, hard);
+    c.valid = need > 0 && need <= hard;
+    return c;
+}
+
+template <typename T>
+static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sino, float *acc, void *vol,
+                         cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)p.vol_elems * p.batch, st);
+    if (e != cudaSuccess) return (int)e;
+    const size_t smem = sizeof(float) * (size_t)c.box_cap;
+    e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    const int per_launch = 65535 / p.n_views > 0 ? 65535 / p.n_views : 1;
+    for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
+        const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
+        dim3 grid(ceil_div(p.det.nu, AS_TU), ceil_div(p.det.nv, AS_TV), p.n_views * nb);
+        adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(p, c.depth, c.guard, c.box_cap,
+                                                          (const T *)sino + b0 * p.sino_elems, acc + b0 * p.vol_elems);
+    }
+    if ((void *)acc != vol) {
+        const long long n = p.vol_elems * p.batch;
+        const int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+        adjoint_convert_kernel<T><<<blocks, 256, 0, st>>>(acc, (T *)vol, n);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino, void *vol, float *acc32, int dtype,
+                        void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_slab_t<float>(p, c, sino, (float *)vol, vol, st);
+        case PYRONN_BF16: return launch_slab_t<__nv_bfloat16>(p, c, sino, acc32, vol, st);
+        case PYRONN_F16: return launch_slab_t<__half>(p, c, sino, acc32, vol, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pyronn

@@ -21,6 +21,7 @@
 #include <thread>
 
 #include "device_common.cuh"
+#include "host_rays.h"
 
 namespace pyronn {
 
@@ -211,29 +212,6 @@ __global__ void __launch_bounds__(TU *TV) fp_slab_kernel(OpParams p, FpSlabCfg c
 // ---------------------------------------------------------------------------------------------
 namespace {
 
-struct RayD {
-    double c[3], d[3];
-};
-
-// FP64 version of ray_setup (same construction, unrounded).
-RayD ray_setup_d(const FpRec &r, const pyronn_geom *g, double u, double v) {
-    double Y[3], D[3];
-    for (int i = 0; i < 3; ++i) {
-        Y[i] = (double)r.R0[i] + u * r.Ru[i] + v * r.Rv[i];
-        D[i] = (double)r.B0[i] + u * r.Bu[i] + v * r.Bv[i];
-    }
-    double inv = 1.0 / std::sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-    for (int i = 0; i < 3; ++i) D[i] *= inv;
-    double tau = -(Y[0] * D[0] + Y[1] * D[1] + Y[2] * D[2]);
-    const double is[3] = {1.0 / g->sx, 1.0 / g->sy, 1.0 / g->sz};
-    const double h[3] = {0.5 * (g->nx - 1), 0.5 * (g->ny - 1), 0.5 * (g->nz - 1)};
-    RayD o;
-    for (int i = 0; i < 3; ++i) {
-        o.c[i] = (Y[i] + tau * D[i]) * is[i] + h[i];
-        o.d[i] = D[i] * is[i];
-    }
-    return o;
-}
 
 // Upper bound of the staged box (in elements) of one tile over all its slabs. The extent of a
 // linear function's range over the corner rays is convex in the plane position, so the first

@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "device_common.cuh"
+#include "host_rays.h"
 
 namespace pyronn {
 
@@ -398,28 +399,6 @@ __global__ void __launch_bounds__(TMA_NT, 2) fp_tma_batched_kernel(const __grid_
 // ---------------------------------------------------------------------------------------------
 namespace {
 
-struct RayD {
-    double c[3], d[3];
-};
-
-RayD ray_setup_d(const FpRec &r, const pyronn_geom *g, double u, double v) {
-    double Y[3], D[3];
-    for (int i = 0; i < 3; ++i) {
-        Y[i] = (double)r.R0[i] + u * r.Ru[i] + v * r.Rv[i];
-        D[i] = (double)r.B0[i] + u * r.Bu[i] + v * r.Bv[i];
-    }
-    double inv = 1.0 / std::sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-    for (int i = 0; i < 3; ++i) D[i] *= inv;
-    double tau = -(Y[0] * D[0] + Y[1] * D[1] + Y[2] * D[2]);
-    const double is[3] = {1.0 / g->sx, 1.0 / g->sy, 1.0 / g->sz};
-    const double h[3] = {0.5 * (g->nx - 1), 0.5 * (g->ny - 1), 0.5 * (g->nz - 1)};
-    RayD o;
-    for (int i = 0; i < 3; ++i) {
-        o.c[i] = (Y[i] + tau * D[i]) * is[i] + h[i];
-        o.d[i] = D[i] * is[i];
-    }
-    return o;
-}
 
 // Per march axis, the largest cross-axis extents (in voxels) of any tile's staged box.
 void tile_extents(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0, int D, int G, int base0,

@@ -76,6 +76,15 @@ const FpSlabCfg &fp_cfg(pyronn_geom_t g) {
     return g->fp_cfg;
 }
 
+const AdjSlabCfg &adj_cfg(pyronn_geom_t g) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (!g->adj_cfg_ready) {
+        g->adj_cfg = choose_adj_slab_cfg(g);
+        g->adj_cfg_ready = 1;
+    }
+    return g->adj_cfg;
+}
+
 const FpTmaBox &tma_cfg(pyronn_geom_t g, int dtype) {
     std::lock_guard<std::mutex> lk(g->mu);
     if (!g->tma_ready[dtype]) {
@@ -131,6 +140,19 @@ int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out) {
     return PYRONN_OK;
 }
 
+int pyronn_geom_adjoint_config(pyronn_geom_t g, int *out) {
+    clear_error();
+    if (!g || !out) return set_error(PYRONN_INVALID_ARG, "null argument");
+    const AdjSlabCfg &ac = adj_cfg(g);
+    int kernel = g->adj_variant == 1 ? 1 : 2;
+    if ((g->adj_variant == 0 || g->adj_variant == 3) && ac.valid) kernel = 3;
+    out[0] = kernel;
+    out[1] = ac.depth;
+    out[2] = ac.guard;
+    out[3] = ac.box_cap;
+    return PYRONN_OK;
+}
+
 int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
@@ -155,7 +177,7 @@ int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
     if (op < 0 || op > 2) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
-    if (variant < 0 || variant > (op == 0 ? 3 : 2)) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
+    if (variant < 0 || variant > (op == 2 ? 2 : 3)) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
     if (op == 0) g->fp_variant = variant;
     else if (op == 1) g->adj_variant = variant;
     else g->bp_variant = variant;
@@ -168,6 +190,17 @@ int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int dtype, int 
     if (rc) return rc;
     if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
     OpParams p = make_params(g, batch);
+    if (g->adj_variant == 0 || g->adj_variant == 3) {
+        const AdjSlabCfg &ac = adj_cfg(g);
+        if (ac.valid) {
+            float *acc = nullptr;
+            if (dtype != PYRONN_F32) {
+                if ((rc = ensure_scratch(g, sizeof(float) * (size_t)p.vol_elems * batch))) return rc;
+                acc = (float *)g->d_scratch;
+            }
+            return cuda_rc(launch_adjoint_slab(p, ac, sino, vol, acc, dtype, stream), "adjoint launch");
+        }
+    }
     if (g->adj_variant != 1) return cuda_rc(launch_adjoint_brick(p, sino, vol, dtype, stream), "adjoint launch");
     float *acc = nullptr;
     if (dtype != PYRONN_F32) {

@@ -88,6 +88,13 @@ struct FpTmaBox {
     int nbuf;                  // 1 or 2 shared-memory buffers
 };
 
+// Slab-ordered adjoint configuration (chosen per geometry).
+struct AdjSlabCfg {
+    int depth, guard;          // slab depth, guard planes
+    int box_cap;               // shared-memory box capacity (floats)
+    int valid;                 // 0: use the brick adjoint
+};
+
 // Batched (persistent) launches: per-volume descriptions of one plan, in processing order.
 constexpr int PLAN_MAX = 16;
 struct PlanVolume {
@@ -153,7 +160,9 @@ struct pyronn_geom {
     pyronn::Tuning tuning;
     int tma_ready[3] = {0, 0, 0};
     int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged (thread loads), 3 slab-staged (TMA)
-    int adj_variant = 0;           // 0 auto, 1 atomic scatter, 2 output-stationary bricks
+    int adj_variant = 0;           // 0 auto, 1 atomic scatter, 2 output-stationary bricks, 3 slab-ordered
+    pyronn::AdjSlabCfg adj_cfg{};
+    int adj_cfg_ready = 0;
     int bp_variant = 0;            // 0 auto, 1 one thread per voxel (absolute coordinates), 2 bricks
 };
 
@@ -182,6 +191,9 @@ int launch_fp(const OpParams &p, const FpSlabCfg &cfg, const void *vol, void *si
 int launch_fp_direct(const OpParams &p, const void *vol, void *sino, int dtype, void *stream);
 int launch_adjoint(const OpParams &p, const void *sino, void *vol, float *acc32, int dtype, void *stream);
 int launch_adjoint_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
+AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g);
+int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino, void *vol, float *acc32, int dtype,
+                        void *stream);
 int launch_adjoint_scatter_acc(const OpParams &p, const void *sino, float *acc, void *vol, int dtype, void *stream);
 int launch_bp(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);

@@ -171,6 +171,11 @@ class Geometry:
                 "box": [o[4:7], o[7:10], o[10:13]], "buf_elems": o[13], "smem_bytes": o[14],
                 "thread_box_capacity": o[15]}
 
+    def adjoint_config(self) -> dict:
+        out = (ctypes.c_int * 4)()
+        check(lib().pyronn_geom_adjoint_config(self._h, out))
+        return {"kernel": out[0], "depth": out[1], "guard": out[2], "box_floats": out[3]}
+
     def set_tuning(self, param: int, value: int) -> None:
         check(lib().pyronn_geom_set_tuning(self._h, int(param), int(value)))
 

@@ -73,7 +73,7 @@ def test_fp_matches_oracle(ops, case, variant):
     assert g.read_flags()[:4] == [0, 0, 0, 0]
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
 def test_adjoint_matches_oracle(ops, case, variant):
     g = case.library_geometry()
@@ -83,6 +83,7 @@ def test_adjoint_matches_oracle(ops, case, variant):
     a = host(ops.adjoint(to_dev(y.reshape((og.n_views, -1)) if case.ndim == 2 else y), g))
     ref = oracle.adjoint(og, y)
     assert rel_l2(a.reshape(ref.shape), ref) <= 1e-5
+    assert g.read_flags()[:4] == [0, 0, 0, 0]
 
 
 @pytest.mark.parametrize("variant", [1, 2])
