@@ -239,8 +239,15 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * settings compute the same operator. PYRONN_TUNE_FP_DEPTH: slab depth of the TMA-staged forward
  * projector in voxel planes (rounded up to the 16-byte x alignment); PYRONN_TUNE_FP_BUFFERS: 1 or
  * 2 shared-memory slab buffers (2 overlaps the next copy with sampling; 1 halves shared memory so
- * more CTAs fit on an SM). */
-typedef enum { PYRONN_TUNE_FP_DEPTH = 0, PYRONN_TUNE_FP_BUFFERS = 1 } pyronn_tuning_param;
+ * more CTAs fit on an SM); PYRONN_TUNE_ADJ_ACCUM: accumulation of the slab-ordered adjoint's
+ * shared-memory boxes, 0 automatic (int32 fixed point with a power-of-two scale per tile and slab
+ * wherever a bound on the box values keeps the quantum at or below 2^-23 of the tile's largest
+ * contribution, FP32 reductions elsewhere), 1 FP32 reductions only. */
+typedef enum {
+    PYRONN_TUNE_FP_DEPTH = 0,
+    PYRONN_TUNE_FP_BUFFERS = 1,
+    PYRONN_TUNE_ADJ_ACCUM = 2
+} pyronn_tuning_param;
 PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
 
 /* ------------------------------------------------------------------------------------------
@@ -251,8 +258,9 @@ PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
  * the slab-staged projector that fell outside their staged box and were read from global memory
  * instead, [1] rays sampled outside the slab march (nearly parallel to the slabs), [2] slabs whose
  * box exceeded shared memory, [3] tensor copies that did not complete within the bounded wait (the
- * launch then stops early and its output is invalid). Synchronous (device-wide copy). All zero is
- * the expected state. */
+ * launch then stops early and its output is invalid); all zero is the expected state of [0..3].
+ * [4], [5]: (tile, slab) boxes of the slab-ordered adjoint accumulated in int32 fixed point and in
+ * FP32 (information, not errors). Synchronous (device-wide copy). */
 PYRONN_API int pyronn_geom_read_flags(pyronn_geom_t g, int *out, int reset);
 
 /* Forward-projector configuration that would be used for element type dtype (host computation,

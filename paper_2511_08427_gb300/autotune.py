@@ -16,8 +16,7 @@ import numpy as np
 import torch
 
 from ._lib import PyronnError
-
-FP_DEPTH, FP_BUFFERS = 0, 1
+from .operators import TUNE_FP_BUFFERS as FP_BUFFERS, TUNE_FP_DEPTH as FP_DEPTH
 
 DEFAULT_CANDIDATES = [(8, 2), (8, 1), (4, 2), (4, 1), (12, 1), (16, 1)]
 

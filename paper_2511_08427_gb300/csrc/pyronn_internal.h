@@ -69,7 +69,15 @@ struct OpParams {
 constexpr int VIEW64_STRIDE = 32;
 
 // Diagnostic counters (device, per geometry).
-enum { FLAG_SLAB_OUT_OF_BOX = 0, FLAG_SLAB_DIRECT_RAY = 1, FLAG_SLAB_OVERFLOW = 2, FLAG_TMA_TIMEOUT = 3, N_FLAGS = 8 };
+enum {
+    FLAG_SLAB_OUT_OF_BOX = 0,
+    FLAG_SLAB_DIRECT_RAY = 1,
+    FLAG_SLAB_OVERFLOW = 2,
+    FLAG_TMA_TIMEOUT = 3,
+    FLAG_ADJ_FIXED_SLABS = 4,
+    FLAG_ADJ_FLOAT_SLABS = 5,
+    N_FLAGS = 8
+};
 
 // Launch configuration of the slab-staged forward projector (chosen per geometry).
 struct FpSlabCfg {
@@ -93,6 +101,7 @@ struct AdjSlabCfg {
     int depth, guard;          // slab depth, guard planes
     int box_cap;               // shared-memory box capacity (floats)
     int valid;                 // 0: use the brick adjoint
+    int allow_fixed;           // int32 fixed-point boxes where the per-slab bound allows
 };
 
 // Batched (persistent) launches: per-volume descriptions of one plan, in processing order.
@@ -118,6 +127,7 @@ struct PlanLaunch {
 struct Tuning {
     int fp_depth = 0;          // slab depth of the TMA forward projector
     int fp_nbuf = 0;           // its number of buffers
+    int adj_accum = 0;         // slab adjoint boxes: 0 automatic, 1 FP32 only
 };
 
 }  // namespace pyronn

@@ -22,6 +22,9 @@ from ._lib import BF16, BP_INV_W2, BP_PLAIN, F16, F32, DetDesc, VolDesc, check, 
 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
+# tuning parameters of Geometry.set_tuning (pyronn_tuning_param)
+TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM = 0, 1, 2
+
 
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
