@@ -242,7 +242,9 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * more CTAs fit on an SM); PYRONN_TUNE_ADJ_ACCUM: accumulation of the slab-ordered adjoint's
  * shared-memory boxes, 0 automatic (int32 fixed point with a power-of-two scale per tile and slab
  * wherever a bound on the box values keeps the quantum at or below 2^-23 of the tile's largest
- * contribution, FP32 reductions elsewhere), 1 FP32 reductions only. */
+ * contribution, FP32 reductions elsewhere; fixed-point boxes take one reduction per sample and
+ * corner), 1 FP32 reductions only, 2 as 0 but fixed-point boxes take one reduction per corner of
+ * each cell a ray passes (weights summed in registers while the ray stays in the cell). */
 typedef enum {
     PYRONN_TUNE_FP_DEPTH = 0,
     PYRONN_TUNE_FP_BUFFERS = 1,

@@ -83,8 +83,32 @@ __device__ __forceinline__ void as_red_shared(unsigned addr, float v) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v));
 }
 
-__device__ __forceinline__ void as_red_shared_fx(unsigned addr, float v, float scale) {
-    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(__float2int_rn(v * scale)));
+__device__ __forceinline__ void as_red_shared_s32(unsigned addr, int v) {
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+// Floor and fraction without the range clamp, for positions inside a slab box (|q| far below 2^22);
+// a position outside that range gives an index outside the box, which the caller's bounds test routes
+// to the checked global path.
+__device__ __forceinline__ void as_floor_frac_unclamped(float q, int &i, float &f) {
+    const float M = 12582912.0f;
+    const float t = __fadd_rd(q, M);
+    i = __float_as_int(t) - 0x4B400000;
+    f = q - (t - M);
+}
+
+// A cell whose 2 x 2 x 2 corner block (volume index of corner 0: gx, gy, gz) does not lie in the box:
+// never expected (the box covers the tile's frustum); the corners inside the volume are added to
+// global memory (values times unscale) and counted.
+__device__ __noinline__ void as_out_of_box(const OpParams &p, float *vb, int gx, int gy, int gz, const float *vals,
+                                           float unscale) {
+    for (int c = 0; c < 8; ++c) {
+        const int x = gx + (c & 1), y = gy + ((c >> 1) & 1), z = gz + (c >> 2);
+        if ((unsigned)x < (unsigned)p.vol.nx && (unsigned)y < (unsigned)p.vol.ny && (unsigned)z < (unsigned)p.vol.nz) {
+            atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
+            atomicAdd(vb + ((long long)z * p.vol.ny + y) * p.vol.nx + x, vals[c] * unscale);
+        }
+    }
 }
 
 // Power-of-two scale for a box whose values are bounded by bound (> 0): bound 2^e <= 2^30.
@@ -241,7 +265,8 @@ __device__ __forceinline__ void as_ray_dir(const AsTile &T, float fu, float fv, 
 
 template <typename T>
 __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int depth, int guard, int box_cap,
-                                                                int allow_fixed, const T *__restrict__ sino,
+                                                                int allow_fixed, int cell_fixed,
+                                                                const T *__restrict__ sino,
                                                                 float *__restrict__ vol) {
     extern __shared__ __align__(16) float box[];
     __shared__ AsShared sh;
@@ -395,6 +420,9 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
     const unsigned box_base = (unsigned)__cvta_generic_to_shared(box);
     const float isx = p.vol.isx, isy = p.vol.isy, isz = p.vol.isz;
     const bool vec4 = (p.vol.nx & 3) == 0;
+    const float inv_dt = 1.0f / dt;
+    const float sxv = (float)p.sx, syv = (float)p.sy, szv = (float)p.sz;
+    const float hxv = 0.5f * (p.vol.nx - 1), hyv = 0.5f * (p.vol.ny - 1), hzv = 0.5f * (p.vol.nz - 1);
 
     for (int i = 0; i < nsl; ++i) {
         const AsSlab &S = sh.slab[i];
@@ -405,8 +433,10 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
             if (tid == 0) atomicAdd(p.flags + FLAG_SLAB_OVERFLOW, 1);
         }
         const int Ex = S.ext[0], Ey = S.ext[1], Ez = S.ext[2];
-        const float sc = S.scale, isc = S.inv_scale;
-        const bool fx = sc != 0.0f;
+        const float isc = S.inv_scale;
+        const bool fx = S.scale != 0.0f;
+        const float ysc = fx ? S.scale : 1.0f;
+        const bool per_sample = fx && !cell_fixed;
         const int lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2];
         const unsigned sy4 = 4u * (unsigned)Ex, sz4 = 4u * (unsigned)(Ex * Ey);
         const int nbox = Ex * Ey * Ez;
@@ -494,18 +524,49 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
             // global FP32 estimate of s for sample ka, rounded to the lattice of the local phase
             const float qcx = fmaf(tka, r.dx, r.cx), qcy = fmaf(tka, r.dy, r.cy), qcz = fmaf(tka, r.dz, r.cz);
             // s of sample ka: projection onto d of (X_ka - (X_s + P)) in world mm
-            const float hx = 0.5f * (p.vol.nx - 1), hy = 0.5f * (p.vol.ny - 1), hz = 0.5f * (p.vol.nz - 1);
-            const float wx = (qcx - hx) / isx - (S.Xs[0] + P0);
-            const float wy = (qcy - hy) / isy - (S.Xs[1] + P1);
-            const float wz = (qcz - hz) / isz - (S.Xs[2] + P2);
+            const float wx = fmaf(qcx - hxv, sxv, -(S.Xs[0] + P0));
+            const float wy = fmaf(qcy - hyv, syv, -(S.Xs[1] + P1));
+            const float wz = fmaf(qcz - hzv, szv, -(S.Xs[2] + P2));
             const float s_est = fmaf(wx, d[0], fmaf(wy, d[1], wz * d[2]));
-            const float jf = rintf((s_est + e) / dt - 0.5f + S.f);   // k - K for sample ka
+            const float jf = rintf(fmaf(s_est + e, inv_dt, S.f - 0.5f));   // k - K for sample ka
             const float c_r = (0.5f - S.f) * dt - e;
             const float qP0 = fmaf(P0, isx, S.o[0]), qP1 = fmaf(P1, isy, S.o[1]), qP2 = fmaf(P2, isz, S.o[2]);
             const float qd0 = d[0] * isx, qd1 = d[1] * isy, qd2 = d[2] * isz;
+            const float ys = y * ysc;   // fixed point: y dt 2^e; FP32 boxes: y dt
+            float jj = jf;
+            if (per_sample) {
+                // int32 boxes: every sample adds its eight corner weights, no cell bookkeeping
+                for (int k = ka; k <= kb; ++k, jj += 1.0f) {
+                    const float sj = fmaf(jj, dt, c_r);
+                    int ix, iy, iz;
+                    float ax, ay, az;
+                    as_floor_frac_unclamped(fmaf(sj, qd0, qP0), ix, ax);
+                    as_floor_frac_unclamped(fmaf(sj, qd1, qP1), iy, ay);
+                    as_floor_frac_unclamped(fmaf(sj, qd2, qP2), iz, az);
+                    const float wz1 = ys * az, wz0 = ys - wz1;
+                    const float oay = 1.f - ay, oax = 1.f - ax;
+                    const float w00 = wz0 * oay, w01 = wz0 * ay, w10 = wz1 * oay, w11 = wz1 * ay;
+                    if ((unsigned)ix < (unsigned)(Ex - 1) && (unsigned)iy < (unsigned)(Ey - 1) &&
+                        (unsigned)iz < (unsigned)(Ez - 1)) {
+                        const unsigned a = box_base + 4u * (unsigned)((iz * Ey + iy) * Ex + ix);
+                        as_red_shared_s32(a, __float2int_rn(w00 * oax));
+                        as_red_shared_s32(a + 4u, __float2int_rn(w00 * ax));
+                        as_red_shared_s32(a + sy4, __float2int_rn(w01 * oax));
+                        as_red_shared_s32(a + sy4 + 4u, __float2int_rn(w01 * ax));
+                        as_red_shared_s32(a + sz4, __float2int_rn(w10 * oax));
+                        as_red_shared_s32(a + sz4 + 4u, __float2int_rn(w10 * ax));
+                        as_red_shared_s32(a + sz4 + sy4, __float2int_rn(w11 * oax));
+                        as_red_shared_s32(a + sz4 + sy4 + 4u, __float2int_rn(w11 * ax));
+                    } else {
+                        const float vals[8] = {w00 * oax, w00 * ax, w01 * oax, w01 * ax,
+                                               w10 * oax, w10 * ax, w11 * oax, w11 * ax};
+                        as_out_of_box(p, vb, ix + lo0, iy + lo1, iz + lo2, vals, isc);
+                    }
+                }
+                continue;
+            }
             float a0 = 0.f, a1v = 0.f, a2v = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f, a7 = 0.f;
             int pix = 0, piy = 0, piz = 0, pkey = -1;
-            float jj = jf;
             for (int k = ka; k <= kb + 1; ++k, jj += 1.0f) {
                 int key = -2, ix = 0, iy = 0, iz = 0;
                 float ax = 0.f, ay = 0.f, az = 0.f;
@@ -524,14 +585,14 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
                             // volume land in the box margin and are dropped when the box is added)
                             const unsigned a = box_base + 4u * (unsigned)((piz * Ey + piy) * Ex + pix);
                             if (fx) {
-                                as_red_shared_fx(a, a0, sc);
-                                as_red_shared_fx(a + 4u, a1v, sc);
-                                as_red_shared_fx(a + sy4, a2v, sc);
-                                as_red_shared_fx(a + sy4 + 4u, a3, sc);
-                                as_red_shared_fx(a + sz4, a4, sc);
-                                as_red_shared_fx(a + sz4 + 4u, a5, sc);
-                                as_red_shared_fx(a + sz4 + sy4, a6, sc);
-                                as_red_shared_fx(a + sz4 + sy4 + 4u, a7, sc);
+                                as_red_shared_s32(a, __float2int_rn(a0));
+                                as_red_shared_s32(a + 4u, __float2int_rn(a1v));
+                                as_red_shared_s32(a + sy4, __float2int_rn(a2v));
+                                as_red_shared_s32(a + sy4 + 4u, __float2int_rn(a3));
+                                as_red_shared_s32(a + sz4, __float2int_rn(a4));
+                                as_red_shared_s32(a + sz4 + 4u, __float2int_rn(a5));
+                                as_red_shared_s32(a + sz4 + sy4, __float2int_rn(a6));
+                                as_red_shared_s32(a + sz4 + sy4 + 4u, __float2int_rn(a7));
                             } else {
                                 as_red_shared(a, a0);
                                 as_red_shared(a + 4u, a1v);
@@ -543,18 +604,8 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
                                 as_red_shared(a + sz4 + sy4 + 4u, a7);
                             }
                         } else {
-                            // outside the box: never expected (the box covers the tile's frustum); corners
-                            // inside the volume go to global memory and are counted
                             const float vals[8] = {a0, a1v, a2v, a3, a4, a5, a6, a7};
-                            for (int c = 0; c < 8; ++c) {
-                                const int gx = pix + (c & 1) + lo0, gy = piy + ((c >> 1) & 1) + lo1,
-                                          gz = piz + (c >> 2) + lo2;
-                                if ((unsigned)gx < (unsigned)p.vol.nx && (unsigned)gy < (unsigned)p.vol.ny &&
-                                    (unsigned)gz < (unsigned)p.vol.nz) {
-                                    atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
-                                    atomicAdd(vb + ((long long)gz * p.vol.ny + gy) * p.vol.nx + gx, vals[c]);
-                                }
-                            }
+                            as_out_of_box(p, vb, pix + lo0, piy + lo1, piz + lo2, vals, fx ? isc : 1.0f);
                         }
                     }
                     a0 = a1v = a2v = a3 = a4 = a5 = a6 = a7 = 0.f;
@@ -562,7 +613,7 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
                     pix = ix; piy = iy; piz = iz;
                 }
                 if (k <= kb) {
-                    const float wz1 = y * az, wz0 = y - wz1;
+                    const float wz1 = ys * az, wz0 = ys - wz1;
                     const float w00 = wz0 * (1.f - ay), w01 = wz0 * ay, w10 = wz1 * (1.f - ay), w11 = wz1 * ay;
                     a0 = fmaf(w00, 1.f - ax, a0);
                     a1v = fmaf(w00, ax, a1v);
@@ -708,6 +759,7 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     c.box_cap = (int)std::min(need, hard);
     c.valid = need > 0 && need <= hard;
     c.allow_fixed = g->tuning.adj_accum != 1;
+    c.cell_fixed = g->tuning.adj_accum == 2;
     return c;
 }
 
@@ -723,7 +775,7 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
     for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
         const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
         dim3 grid(ceil_div(p.det.nu, AS_TU), ceil_div(p.det.nv, AS_TV), p.n_views * nb);
-        adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(p, c.depth, c.guard, c.box_cap, c.allow_fixed,
+        adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(p, c.depth, c.guard, c.box_cap, c.allow_fixed, c.cell_fixed,
                                                           (const T *)sino + b0 * p.sino_elems, acc + b0 * p.vol_elems);
     }
     if ((void *)acc != vol) {

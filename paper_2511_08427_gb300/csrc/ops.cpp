@@ -167,7 +167,7 @@ int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
             g->tuning.fp_nbuf = value;
             break;
         case PYRONN_TUNE_ADJ_ACCUM:
-            if (value < 0 || value > 1) return set_error(PYRONN_INVALID_ARG, "accumulation mode %d out of [0, 1]", value);
+            if (value < 0 || value > 2) return set_error(PYRONN_INVALID_ARG, "accumulation mode %d out of [0, 2]", value);
             g->tuning.adj_accum = value;
             g->adj_cfg_ready = 0;
             break;

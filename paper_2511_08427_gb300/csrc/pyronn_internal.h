@@ -102,6 +102,7 @@ struct AdjSlabCfg {
     int box_cap;               // shared-memory box capacity (floats)
     int valid;                 // 0: use the brick adjoint
     int allow_fixed;           // int32 fixed-point boxes where the per-slab bound allows
+    int cell_fixed;            // fixed-point boxes: 1 cell-accumulated reductions, 0 one per sample
 };
 
 // Batched (persistent) launches: per-volume descriptions of one plan, in processing order.
@@ -127,7 +128,7 @@ struct PlanLaunch {
 struct Tuning {
     int fp_depth = 0;          // slab depth of the TMA forward projector
     int fp_nbuf = 0;           // its number of buffers
-    int adj_accum = 0;         // slab adjoint boxes: 0 automatic, 1 FP32 only
+    int adj_accum = 0;         // slab adjoint boxes: 0 automatic, 1 FP32 only, 2 fixed point with cells
 };
 
 }  // namespace pyronn

@@ -1,13 +1,13 @@
 """Run one operator on a cone-beam workload a few times (for profilers such as Nsight Compute).
 
     python -m paper_2511_08427_gb300.profile_ops {fp,adj,bp} [N] [--repeat R] [--dtype float32|bfloat16]
-                                                 [--accum 0|1] [--time]
+                                                 [--accum 0|1|2] [--time]
 
 N = 256: 256^3 volume (0.5 mm voxels), 360 views over 2 pi, 512 x 512 detector (0.6 mm),
 SID 750 mm, SDD 1200 mm, 20 random ellipsoids (seed 3). Smaller N keeps the same field of view
 and magnification with N^3 voxels, 180 views and a 2N x 2N detector. Prints the device counters;
 --time also prints the mean CUDA-event time of the repeats after one warm-up launch. --accum sets
-the slab adjoint's box accumulation (0 automatic, 1 FP32 only).
+the slab adjoint's box accumulation (0 automatic, 1 FP32 only, 2 fixed point with cells).
 """
 from __future__ import annotations
 
@@ -37,7 +37,7 @@ def main():
     ap.add_argument("n", nargs="?", type=int, default=256)
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--dtype", default="float32", choices=["float32", "bfloat16", "float16"])
-    ap.add_argument("--accum", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--accum", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--time", action="store_true")
     a = ap.parse_args()
     dt = getattr(torch, a.dtype)

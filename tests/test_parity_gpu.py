@@ -89,11 +89,12 @@ def test_adjoint_matches_oracle(ops, case, variant):
 SMALL3 = [c for c in SMALL if c.ndim == 3]
 
 
-@pytest.mark.parametrize("accum", [0, 1])
+@pytest.mark.parametrize("accum", [0, 1, 2])
 @pytest.mark.parametrize("case", SMALL3, ids=lambda c: c.name)
 def test_slab_adjoint_accumulation_modes(ops, case, accum):
-    """Slab-ordered adjoint with int32 fixed-point boxes (automatic) and FP32 boxes only: both match
-    the oracle; the diagnostic counters say which boxes were used."""
+    """Slab-ordered adjoint with int32 fixed-point boxes (automatic: per-sample reductions; 2: cell
+    accumulation) and FP32 boxes only: all match the oracle; the diagnostic counters say which boxes
+    were used."""
     g = case.library_geometry()
     g.set_variant(1, 3)
     g.set_tuning(ops.TUNE_ADJ_ACCUM, accum)
