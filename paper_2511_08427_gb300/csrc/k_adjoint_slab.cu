@@ -15,7 +15,11 @@
 // where the tile's corner ray meets the plane through X_s, the per-pixel steps of that point, and
 // the lattice phase of the corner ray at X_s. Each ray then needs only small FP32 quantities.
 //
-// Lanes of a warp take rays 4 pixels apart in u and 8 in v, so their samples rarely share a voxel.
+// Lanes of a warp take the 32 pixels of one tile row. Where the tile marches along x, every lane sits
+// at nearly the same x index at a given step, so with 16-byte row pitches all lanes would hit one word
+// of each 16-byte bank group; there each group of 8 lanes walks its slab samples starting 3 samples
+// later than the previous group (cyclically), which spreads the reductions over the banks. Integer
+// additions commute exactly, so the order does not change fixed-point results.
 //
 // Box accumulation: shared-memory FP32 reductions are a load / compare-and-swap sequence on this
 // GPU, integer reductions a single operation (about 3.6x the throughput). Where a bound allows, a
@@ -56,6 +60,7 @@ struct AsSlab {                 // per (tile, slab), relative to the box centre 
     float Xs[3];                // X_s - C (world mm)
     float o[3];                 // box-local index of X_s
     float f;                    // phase of the corner ray at X_s: (X_s - C) . dref = (K + f) dt
+    int K;
     int lo[3], ext[3];          // box origin and extents (voxels); ext[0] == 0: empty slab
     float scale, inv_scale;     // fixed-point scale 2^e and 2^-e; scale == 0: FP32 box
 };
@@ -95,6 +100,25 @@ __device__ __forceinline__ void as_floor_frac_unclamped(float q, int &i, float &
     const float t = __fadd_rd(q, M);
     i = __float_as_int(t) - 0x4B400000;
     f = q - (t - M);
+}
+
+// Samples k0..k1 of a global FP32 ray (index coordinates) added straight to the volume with global
+// atomics (rays nearly parallel to the slabs, and slabs whose box does not fit).
+__device__ __noinline__ void as_scatter_global(const OpParams &p, float *vb, const RayIdx r, int k0, int k1, float y) {
+    for (int k = k0; k <= k1; ++k) {
+        const float t = fmaf((float)k, p.dt, 0.5f * p.dt);
+        const float qx = fmaf(t, r.dx, r.cx), qy = fmaf(t, r.dy, r.cy), qz = fmaf(t, r.dz, r.cz);
+        const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+        const float ax = qx - fx, ay = qy - fy, az = qz - fz;
+        for (int c = 0; c < 8; ++c) {
+            const int cx = ix + (c & 1), cy = iy + ((c >> 1) & 1), cz = iz + (c >> 2);
+            if ((unsigned)cx < (unsigned)p.vol.nx && (unsigned)cy < (unsigned)p.vol.ny && (unsigned)cz < (unsigned)p.vol.nz) {
+                const float w = ((c & 1) ? ax : 1.0f - ax) * (((c >> 1) & 1) ? ay : 1.0f - ay) * ((c >> 2) ? az : 1.0f - az);
+                atomicAdd(vb + ((long long)cz * p.vol.ny + cy) * p.vol.nx + cx, y * w);
+            }
+        }
+    }
 }
 
 // A cell whose 2 x 2 x 2 corner block (volume index of corner 0: gx, gy, gz) does not lie in the box:
@@ -211,7 +235,9 @@ __device__ void as_slab_setup(const OpParams &p, int view, int u0, int v0, AsSla
         S.Eu[i] = (float)Eu[i];
         S.Ev[i] = (float)Ev[i];
     }
-    S.f = (float)(T - floor(T));
+    const double Kd = floor(T);
+    S.K = (int)Kd;
+    S.f = (float)(T - Kd);
 }
 
 __device__ void as_tile_setup(const OpParams &p, int view, int u0, int v0, AsTile &t) {
@@ -315,32 +341,49 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
     const int base0 = -1;
     const int nslab_all = (Nm + 1 - base0 + D - 1) / D;
 
-    // rays of this thread: lanes 4 pixels apart in u, 8 in v
-    int ru[AS_RPT], rv[AS_RPT];
-#pragma unroll
-    for (int j = 0; j < AS_RPT; ++j) {
-        ru[j] = tu0 + (lane & 7) * 4 + (warp & 3);
-        rv[j] = tv0 + (lane >> 3) * 8 + (warp >> 2) * 4 + j;
-    }
-    // the rays' values y dt, and their maximum over the tile
-    float yv[AS_RPT];
+    // rays of this thread: tile row warp * AS_RPT + j, lanes along u
+    const int rot = m == 0 ? 3 * (lane >> 3) : 0;   // sample-order rotation (bank spreading)
+    // per-ray state kept across slabs: value y dt (0: nothing to scatter), and the global FP32 ray's
+    // march-axis coordinate, inverse step and sample range, which define the slab partition
+    float yv[AS_RPT], rcm[AS_RPT], rinv[AS_RPT];
+    int rk0[AS_RPT], rk1[AS_RPT];
     unsigned ybits = 0u;
 #pragma unroll
     for (int j = 0; j < AS_RPT; ++j) {
-        yv[j] = (ru[j] <= tu1 && rv[j] <= tv1) ? ldg_f32(sb + (long long)rv[j] * p.det.nu + ru[j]) * dt : 0.0f;
+        const int u = tu0 + lane, v = tv0 + warp * AS_RPT + j;
+        yv[j] = (u <= tu1 && v <= tv1) ? ldg_f32(sb + (long long)v * p.det.nu + u) * dt : 0.0f;
         ybits = max(ybits, __float_as_uint(fabsf(yv[j])));
+        rcm[j] = 0.0f;
+        rinv[j] = 0.0f;
+        rk0[j] = 0;
+        rk1[j] = -1;
     }
     ybits = __reduce_max_sync(0xffffffffu, ybits);
     if (lane == 0) atomicMax(&sh.ymax, ybits);
-    // slab range of the tile from the rays' in-box sample ranges
+    // slab range of the tile from the rays' in-box sample ranges; rays barely advancing along m are
+    // scattered straight to global memory here and take no part in the slab march
 #pragma unroll
     for (int j = 0; j < AS_RPT; ++j) {
-        if (ru[j] > tu1 || rv[j] > tv1) continue;
-        RayIdx r = ray_setup(rec, p.vol, (float)ru[j], (float)rv[j]);
+        if (yv[j] == 0.0f) continue;
+        const int u = tu0 + lane, v = tv0 + warp * AS_RPT + j;
+        const RayIdx r = ray_setup(rec, p.vol, (float)u, (float)v);
         int k0, k1;
-        if (!ray_k_range(r, p.vol, dt, k0, k1)) continue;
+        if (!ray_k_range(r, p.vol, dt, k0, k1)) {
+            yv[j] = 0.0f;
+            continue;
+        }
         const float cm = m == 0 ? r.cx : (m == 1 ? r.cy : r.cz);
         const float dm = m == 0 ? r.dx : (m == 1 ? r.dy : r.dz);
+        if (!(fabsf(dm) > 1e-3f * (fabsf(r.dx) + fabsf(r.dy) + fabsf(r.dz)))) {
+            atomicAdd(p.flags + FLAG_SLAB_DIRECT_RAY, 1);
+            as_scatter_global(p, vb, r, k0, k1, yv[j]);
+            yv[j] = 0.0f;
+            continue;
+        }
+        rcm[j] = cm;
+        rinv[j] = 1.0f / (dt * dm);
+        rk0[j] = k0;
+        rk1[j] = k1;
         const float qa = fmaf(fmaf((float)k0, dt, 0.5f * dt), dm, cm);
         const float qb = fmaf(fmaf((float)k1, dt, 0.5f * dt), dm, cm);
         const float qlo = fmaxf(fminf(qa, qb), -1.0f), qhi = fminf(fmaxf(qa, qb), (float)Nm);
@@ -350,6 +393,9 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
         atomicMin(&sh.srange[0], slo);
         atomicMax(&sh.srange[1], shi);
     }
+    // the box starts all zero; each flush zeroes what it added, so it is zero again for the next slab
+    for (int e = 4 * tid; e + 3 < box_cap; e += 4 * AS_NT) *reinterpret_cast<float4 *>(box + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = (box_cap & ~3) + tid; e < box_cap; e += AS_NT) box[e] = 0.0f;
     __syncthreads();
     const int s_first = sh.srange[0];
     const int nsl = sh.srange[1] >= s_first ? min(sh.srange[1] - s_first + 1, AS_MAX_SLABS) : 0;
@@ -420,9 +466,6 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
     const unsigned box_base = (unsigned)__cvta_generic_to_shared(box);
     const float isx = p.vol.isx, isy = p.vol.isy, isz = p.vol.isz;
     const bool vec4 = (p.vol.nx & 3) == 0;
-    const float inv_dt = 1.0f / dt;
-    const float sxv = (float)p.sx, syv = (float)p.sy, szv = (float)p.sz;
-    const float hxv = 0.5f * (p.vol.nx - 1), hyv = 0.5f * (p.vol.ny - 1), hzv = 0.5f * (p.vol.nz - 1);
 
     for (int i = 0; i < nsl; ++i) {
         const AsSlab &S = sh.slab[i];
@@ -439,77 +482,32 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
         const bool per_sample = fx && !cell_fixed;
         const int lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2];
         const unsigned sy4 = 4u * (unsigned)Ex, sz4 = 4u * (unsigned)(Ex * Ey);
-        const int nbox = Ex * Ey * Ez;
-        for (int e = tid; e < nbox; e += AS_NT) box[e] = 0.0f;
-        __syncthreads();
         const int b_lo = base0 + s * D;
         const int b_hi = min(b_lo + D, Nm);
 #pragma unroll 1
         for (int j = 0; j < AS_RPT; ++j) {
-            const int u = ru[j], v = rv[j];
             const float y = yv[j];
-            if (y == 0.0f) continue;   // includes rays outside the detector
+            if (y == 0.0f) continue;   // rays outside the detector or the volume, zero values, direct rays
+            const int u = tu0 + lane, v = tv0 + warp * AS_RPT + j;
             // slab partition on the global FP32 ray (identical formula for the shared boundaries)
-            const RayIdx r = ray_setup(rec, p.vol, (float)u, (float)v);
-            int k0, k1;
-            if (!ray_k_range(r, p.vol, dt, k0, k1)) continue;
-            const float cm = m == 0 ? r.cx : (m == 1 ? r.cy : r.cz);
-            const float dm = m == 0 ? r.dx : (m == 1 ? r.dy : r.dz);
-            if (!(fabsf(dm) > 1e-3f * (fabsf(r.dx) + fabsf(r.dy) + fabsf(r.dz)))) {
-                // a ray barely advancing along m: scattered directly by the first slab
-                if (i == 0) {
-                    atomicAdd(p.flags + FLAG_SLAB_DIRECT_RAY, 1);
-                    for (int k = k0; k <= k1; ++k) {
-                        const float t = fmaf((float)k, dt, 0.5f * dt);
-                        const float qx = fmaf(t, r.dx, r.cx), qy = fmaf(t, r.dy, r.cy), qz = fmaf(t, r.dz, r.cz);
-                        const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
-                        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-                        const float ax = qx - fx, ay = qy - fy, az = qz - fz;
-                        for (int c = 0; c < 8; ++c) {
-                            const int cx = ix + (c & 1), cy = iy + ((c >> 1) & 1), cz = iz + (c >> 2);
-                            if ((unsigned)cx < (unsigned)p.vol.nx && (unsigned)cy < (unsigned)p.vol.ny &&
-                                (unsigned)cz < (unsigned)p.vol.nz) {
-                                const float w = ((c & 1) ? ax : 1.0f - ax) * (((c >> 1) & 1) ? ay : 1.0f - ay) *
-                                                ((c >> 2) ? az : 1.0f - az);
-                                atomicAdd(vb + ((long long)cz * p.vol.ny + cy) * p.vol.nx + cx, y * w);
-                            }
-                        }
-                    }
-                }
-                continue;
-            }
-            const float inv_step = 1.0f / (dt * dm);
+            const float cm = rcm[j], inv_step = rinv[j];
             int ka, kb;
-            if (dm > 0.0f) {
+            if (inv_step > 0.0f) {
                 ka = (int)ceilf(fmaf((float)b_lo - cm, inv_step, -0.5f));
                 kb = (int)ceilf(fmaf((float)b_hi - cm, inv_step, -0.5f)) - 1;
             } else {
                 ka = (int)floorf(fmaf((float)b_hi - cm, inv_step, -0.5f)) + 1;
                 kb = (int)floorf(fmaf((float)b_lo - cm, inv_step, -0.5f));
             }
-            ka = max(ka, k0);
-            kb = min(kb, k1);
+            ka = max(ka, rk0[j]);
+            kb = min(kb, rk1[j]);
             if (ka > kb) continue;
             if (Ex == 0) {
-                for (int k = ka; k <= kb; ++k) {
-                    const float t = fmaf((float)k, dt, 0.5f * dt);
-                    const float qx = fmaf(t, r.dx, r.cx), qy = fmaf(t, r.dy, r.cy), qz = fmaf(t, r.dz, r.cz);
-                    const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
-                    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-                    const float ax = qx - fx, ay = qy - fy, az = qz - fz;
-                    for (int c = 0; c < 8; ++c) {
-                        const int cx = ix + (c & 1), cy = iy + ((c >> 1) & 1), cz = iz + (c >> 2);
-                        if ((unsigned)cx < (unsigned)p.vol.nx && (unsigned)cy < (unsigned)p.vol.ny &&
-                            (unsigned)cz < (unsigned)p.vol.nz) {
-                            const float w = ((c & 1) ? ax : 1.0f - ax) * (((c >> 1) & 1) ? ay : 1.0f - ay) *
-                                            ((c >> 2) ? az : 1.0f - az);
-                            atomicAdd(vb + ((long long)cz * p.vol.ny + cy) * p.vol.nx + cx, y * w);
-                        }
-                    }
-                }
+                as_scatter_global(p, vb, ray_setup(rec, p.vol, (float)u, (float)v), ka, kb, y);
                 continue;
             }
-            // precise local ray: point on the plane through X_s, unit direction, phase
+            // precise local ray: point P on the plane through X_s, unit direction d, and the offset e
+            // of (X_s + P) . d from the phase T dt of the tile's corner ray (K + f = T)
             const float fu = (float)(u - tu0), fv = (float)(v - tv0);
             float d[3], dd[3];
             as_ray_dir(sh.tile, fu, fv, d, dd);
@@ -518,25 +516,23 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
             const float P2 = fmaf(fv, S.Ev[2], fmaf(fu, S.Eu[2], S.A[2]));
             const float e = fmaf(S.Xs[0], dd[0], fmaf(S.Xs[1], dd[1], S.Xs[2] * dd[2])) +
                             fmaf(P0, d[0], fmaf(P1, d[1], P2 * d[2]));
-            // sample k sits at s = (k - K + 1/2 - f) dt - e along d from P, K = floor of the phase:
-            // the integer part is recovered from the global ray's position of sample ka
-            const float tka = fmaf((float)ka, dt, 0.5f * dt);
-            // global FP32 estimate of s for sample ka, rounded to the lattice of the local phase
-            const float qcx = fmaf(tka, r.dx, r.cx), qcy = fmaf(tka, r.dy, r.cy), qcz = fmaf(tka, r.dz, r.cz);
-            // s of sample ka: projection onto d of (X_ka - (X_s + P)) in world mm
-            const float wx = fmaf(qcx - hxv, sxv, -(S.Xs[0] + P0));
-            const float wy = fmaf(qcy - hyv, syv, -(S.Xs[1] + P1));
-            const float wz = fmaf(qcz - hzv, szv, -(S.Xs[2] + P2));
-            const float s_est = fmaf(wx, d[0], fmaf(wy, d[1], wz * d[2]));
-            const float jf = rintf(fmaf(s_est + e, inv_dt, S.f - 0.5f));   // k - K for sample ka
+            // sample k lies (k + 1/2) dt from the ray's point closest to the volume centre, which is
+            // orthogonal to d, i.e. at s = (k + 1/2) dt - (X_s + P) . d = (k - K + 1/2 - f) dt - e from
+            // X_s + P: sample ka has local index ka - K
+            const float jf = (float)(ka - S.K);
             const float c_r = (0.5f - S.f) * dt - e;
             const float qP0 = fmaf(P0, isx, S.o[0]), qP1 = fmaf(P1, isy, S.o[1]), qP2 = fmaf(P2, isz, S.o[2]);
             const float qd0 = d[0] * isx, qd1 = d[1] * isy, qd2 = d[2] * isz;
             const float ys = y * ysc;   // fixed point: y dt 2^e; FP32 boxes: y dt
-            float jj = jf;
             if (per_sample) {
-                // int32 boxes: every sample adds its eight corner weights, no cell bookkeeping
-                for (int k = ka; k <= kb; ++k, jj += 1.0f) {
+                // int32 boxes: every sample adds its eight corner weights, no cell bookkeeping; the
+                // samples ka..kb are visited from ka + r cyclically
+                const int n = kb - ka + 1;
+                const int r = rot % n;
+                const int wrap = n - r;
+                float jj = jf + (float)r;
+                for (int ii = 0; ii < n; ++ii, jj += 1.0f) {
+                    if (ii == wrap) jj -= (float)n;
                     const float sj = fmaf(jj, dt, c_r);
                     int ix, iy, iz;
                     float ax, ay, az;
@@ -567,6 +563,7 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
             }
             float a0 = 0.f, a1v = 0.f, a2v = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f, a7 = 0.f;
             int pix = 0, piy = 0, piz = 0, pkey = -1;
+            float jj = jf;
             for (int k = ka; k <= kb + 1; ++k, jj += 1.0f) {
                 int key = -2, ix = 0, iy = 0, iz = 0;
                 float ax = 0.f, ay = 0.f, az = 0.f;
@@ -627,32 +624,56 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
             }
         }
         __syncthreads();
-        // add the box to the volume: float4 groups along x, all-zero groups skipped
+        // add the box to the volume (float4 groups along x, all-zero groups skipped) and zero it again;
+        // group indices advance by AS_NT groups per step without divisions
         if (Ex > 0) {
             const int gx4 = Ex >> 2;
             const int ngroups = gx4 * Ey * Ez;
+            const int srow = AS_NT / gx4;
+            const int step_x = AS_NT - srow * gx4, step_y = srow % Ey, step_z = srow / Ey;
+            int xg = tid % gx4;
+            const int row0 = tid / gx4;
+            int ly = row0 % Ey, lz = row0 / Ey;
             for (int gi = tid; gi < ngroups; gi += AS_NT) {
-                const int xg = gi % gx4, row = gi / gx4;
-                const int ly = row % Ey, lz = row / Ey;
-                float4 q = *reinterpret_cast<const float4 *>(box + (row * Ex + 4 * xg));
+                float4 *pb = reinterpret_cast<float4 *>(box) + gi;
+                float4 q = *pb;
+                bool nz;
                 if (fx) {
                     const int4 qi = *reinterpret_cast<const int4 *>(&q);
-                    if ((qi.x | qi.y | qi.z | qi.w) == 0) continue;
-                    q = make_float4(__int2float_rn(qi.x) * isc, __int2float_rn(qi.y) * isc, __int2float_rn(qi.z) * isc,
-                                    __int2float_rn(qi.w) * isc);
-                }
-                if (q.x == 0.f && q.y == 0.f && q.z == 0.f && q.w == 0.f) continue;
-                const int gx = lo0 + 4 * xg, gy = lo1 + ly, gz = lo2 + lz;
-                if ((unsigned)gy >= (unsigned)p.vol.ny || (unsigned)gz >= (unsigned)p.vol.nz) continue;
-                float *dst = vb + ((long long)gz * p.vol.ny + gy) * p.vol.nx + gx;
-                if (vec4 && gx >= 0 && gx + 3 < p.vol.nx) {
-                    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(q.x), "f"(q.y),
-                                 "f"(q.z), "f"(q.w)
-                                 : "memory");
+                    nz = (qi.x | qi.y | qi.z | qi.w) != 0;
+                    q = make_float4(__int2float_rn(qi.x) * isc, __int2float_rn(qi.y) * isc,
+                                    __int2float_rn(qi.z) * isc, __int2float_rn(qi.w) * isc);
                 } else {
-                    const float vv[4] = {q.x, q.y, q.z, q.w};
-                    for (int c = 0; c < 4; ++c)
-                        if ((unsigned)(gx + c) < (unsigned)p.vol.nx && vv[c] != 0.f) atomicAdd(dst + c, vv[c]);
+                    // a group summing to -0 is left as is: adding to -0 is exact
+                    nz = q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f;
+                }
+                if (nz) {
+                    *pb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int gx = lo0 + 4 * xg, gy = lo1 + ly, gz = lo2 + lz;
+                    if ((unsigned)gy < (unsigned)p.vol.ny && (unsigned)gz < (unsigned)p.vol.nz) {
+                        float *dst = vb + ((long long)gz * p.vol.ny + gy) * p.vol.nx + gx;
+                        if (vec4 && gx >= 0 && gx + 3 < p.vol.nx) {
+                            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(q.x),
+                                         "f"(q.y), "f"(q.z), "f"(q.w)
+                                         : "memory");
+                        } else {
+                            const float vv[4] = {q.x, q.y, q.z, q.w};
+                            for (int c = 0; c < 4; ++c)
+                                if ((unsigned)(gx + c) < (unsigned)p.vol.nx && vv[c] != 0.f) atomicAdd(dst + c, vv[c]);
+                        }
+                    }
+                }
+                xg += step_x;
+                int carry = 0;
+                if (xg >= gx4) {
+                    xg -= gx4;
+                    carry = 1;
+                }
+                ly += step_y + carry;
+                lz += step_z;
+                if (ly >= Ey) {
+                    ly -= Ey;
+                    lz += 1;
                 }
             }
         }
