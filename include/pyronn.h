@@ -244,11 +244,15 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * wherever a bound on the box values keeps the quantum at or below 2^-23 of the tile's largest
  * contribution, FP32 reductions elsewhere; fixed-point boxes take one reduction per sample and
  * corner), 1 FP32 reductions only, 2 as 0 but fixed-point boxes take one reduction per corner of
- * each cell a ray passes (weights summed in registers while the ray stays in the cell). */
+ * each cell a ray passes (weights summed in registers while the ray stays in the cell);
+ * PYRONN_TUNE_FP_CTAS_PER_SM: CTAs per SM the TMA-staged forward projector is compiled for, 2 or
+ * 4 (4 caps registers at 64 per thread; automatic: 4 where four CTAs' slab buffers fit in shared
+ * memory). */
 typedef enum {
     PYRONN_TUNE_FP_DEPTH = 0,
     PYRONN_TUNE_FP_BUFFERS = 1,
-    PYRONN_TUNE_ADJ_ACCUM = 2
+    PYRONN_TUNE_ADJ_ACCUM = 2,
+    PYRONN_TUNE_FP_CTAS_PER_SM = 3
 } pyronn_tuning_param;
 PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
 

@@ -82,13 +82,14 @@ struct TmaMaps {
 
 struct SlabBox {
     int lo[3];      // box origin (x aligned for TMA)
-    bool fits;      // the tile's footprint in this slab fits the box
+    int fits;       // the tile's footprint in this slab fits the box
 };
 
 struct FpTmaShared {
     unsigned long long bar[2];
     float corner[5][6];
     int srange[2];
+    SlabBox box[2];   // boxes of the slabs in the two copy slots (written by the issuing thread)
 };
 
 // One detector tile (tile_x, tile_y) of one view of volume b: returns false if a tensor copy was lost
@@ -139,8 +140,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
         m = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
     }
     const int a1 = (m == 0) ? 1 : 0, a2 = (m == 2) ? 1 : 2;
-    const int dims[3] = {p.vol.nx, p.vol.ny, p.vol.nz};
-    const int Nm = dims[m];
+    const int Nm = m == 0 ? p.vol.nx : (m == 1 ? p.vol.ny : p.vol.nz);
+    const int N1 = a1 == 0 ? p.vol.nx : p.vol.ny, N2 = a2 == 1 ? p.vol.ny : p.vol.nz;
     const float cm = m == 0 ? r.cx : (m == 1 ? r.cy : r.cz);
     const float dm = m == 0 ? r.dx : (m == 1 ? r.dy : r.dz);
     const bool marchable = fabsf(dm) > 1e-3f * (fabsf(r.dx) + fabsf(r.dy) + fabsf(r.dz));
@@ -151,7 +152,9 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
     const int D = cfg.depth, G = cfg.guard;
     const int base0 = cfg.slab0;                        // slab s covers floor(q_m) in [base0 + s D, base0 + (s+1) D)
     const int nslab_all = (Nm + 1 - base0 + D - 1) / D; // enough slabs to reach plane Nm - 1
-    const int BXb = cfg.bx[m], BYb = cfg.by[m], BZb = cfg.bz[m];
+    const int BXb = m == 0 ? cfg.bx[0] : (m == 1 ? cfg.bx[1] : cfg.bx[2]);
+    const int BYb = m == 0 ? cfg.by[0] : (m == 1 ? cfg.by[1] : cfg.by[2]);
+    const int BZb = m == 0 ? cfg.bz[0] : (m == 1 ? cfg.bz[1] : cfg.bz[2]);
     const int box_elems = BXb * BYb * BZb;
     const unsigned box_bytes = (unsigned)(sizeof(T) * box_elems);
     const CUtensorMap *tmap = &maps3[m];
@@ -173,14 +176,11 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
     const unsigned bars[2] = {smem_u32(&sh.bar[0]), smem_u32(&sh.bar[1])};
     const int align = 16 / (int)sizeof(T);
 
-    // box of slab s (uniform across the CTA)
+    // box of slab s, computed by the thread that issues the slab's copy and shared through sh.box
     auto slab_box = [&](int s) {
         SlabBox sb;
         const int b_lo = base0 + s * D;
         const int b_hi = min(b_lo + D, Nm);
-        int lo[3], hi[3];
-        lo[m] = b_lo - G;
-        hi[m] = b_hi + G;
         float mn1 = 3e38f, mx1 = -3e38f, mn2 = 3e38f, mx2 = -3e38f;
         const float planes[2] = {(float)(b_lo - G), (float)(b_hi + G)};
 #pragma unroll
@@ -197,16 +197,19 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
             }
         }
         const float gf = (float)(G + 2);
-        mn1 = fmaxf(mn1, -gf); mx1 = fminf(mx1, (float)dims[a1] + gf);
-        mn2 = fmaxf(mn2, -gf); mx2 = fminf(mx2, (float)dims[a2] + gf);
-        lo[a1] = max((int)floorf(mn1) - 1, -1 - G);
-        hi[a1] = min((int)floorf(mx1) + 2, dims[a1] + G);
-        lo[a2] = max((int)floorf(mn2) - 1, -1 - G);
-        hi[a2] = min((int)floorf(mx2) + 2, dims[a2] + G);
+        mn1 = fmaxf(mn1, -gf); mx1 = fminf(mx1, (float)N1 + gf);
+        mn2 = fmaxf(mn2, -gf); mx2 = fminf(mx2, (float)N2 + gf);
+        const int lo1 = max((int)floorf(mn1) - 1, -1 - G), hi1 = min((int)floorf(mx1) + 2, N1 + G);
+        const int lo2 = max((int)floorf(mn2) - 1, -1 - G), hi2 = min((int)floorf(mx2) + 2, N2 + G);
+        const int lom = b_lo - G, him = b_hi + G;
+        // (x, y, z) from (m, a1, a2): m = x -> (m, a1, a2); m = y -> (a1, m, a2); m = z -> (a1, a2, m)
+        const int lx = m == 0 ? lom : lo1, hx = m == 0 ? him : hi1;
+        const int ly = m == 0 ? lo1 : (m == 1 ? lom : lo2), hy = m == 0 ? hi1 : (m == 1 ? him : hi2);
+        const int lz = m == 2 ? lom : lo2, hz = m == 2 ? him : hi2;
         // TMA: the innermost start coordinate must be 16-byte aligned
-        int x0 = lo[0] >= 0 ? (lo[0] / align) * align : -(((-lo[0]) + align - 1) / align) * align;
-        sb.lo[0] = x0; sb.lo[1] = lo[1]; sb.lo[2] = lo[2];
-        sb.fits = (hi[0] - x0 + 1 <= BXb) && (hi[1] - lo[1] + 1 <= BYb) && (hi[2] - lo[2] + 1 <= BZb);
+        const int x0 = lx >= 0 ? (lx / align) * align : -(((-lx) + align - 1) / align) * align;
+        sb.lo[0] = x0; sb.lo[1] = ly; sb.lo[2] = lz;
+        sb.fits = (hx - x0 + 1 <= BXb) && (hy - ly + 1 <= BYb) && (hz - lz + 1 <= BZb);
         return sb;
     };
 
@@ -214,7 +217,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
     const float hdt = 0.5f * p.dt;
     if (nsl > 0) {
         if (tid == 0) {
-            SlabBox sb0 = slab_box(s_first);
+            const SlabBox sb0 = slab_box(s_first);
+            sh.box[0] = sb0;
             mbar_expect_tx(bars[0], box_bytes);
             tma_load_4d(smem_u32(buf0), tmap, bars[0], sb0.lo[0], sb0.lo[1], sb0.lo[2], b);
         }
@@ -223,15 +227,18 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
             const int bi = dbl ? (i & 1) : 0;
             const unsigned parity = ph[bi] & 1u;
             if (dbl && tid == 0 && i + 1 < nsl) {
-                SlabBox sbn = slab_box(s + 1);
+                const SlabBox sbn = slab_box(s + 1);
+                sh.box[(i + 1) & 1] = sbn;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(bars[bi ^ 1], box_bytes);
                 tma_load_4d(smem_u32(bi ? buf0 : buf1), tmap, bars[bi ^ 1], sbn.lo[0], sbn.lo[1], sbn.lo[2], b);
             }
-            const SlabBox sb = slab_box(s);
+            // a copy lost anywhere aborts every CTA at its next slab, so the launch ends promptly (the
+            // flag is read before the wait so that the two latencies overlap)
+            int lost = 0;
+            if (tid == 0) lost = *(volatile int *)(p.flags + FLAG_TMA_TIMEOUT);
             bool ok = mbar_wait_bounded(bars[bi], parity);
-            // a copy lost anywhere aborts every CTA at its next slab, so the launch ends promptly
-            if (tid == 0 && *(volatile int *)(p.flags + FLAG_TMA_TIMEOUT) != 0) ok = false;
+            if (lost != 0) ok = false;
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) atomicAdd(p.flags + FLAG_TMA_TIMEOUT, 1);
                 // wait (bounded) for the copies still in flight before the shared memory goes away
@@ -240,6 +247,7 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 return false;
             }
             ++ph[bi];
+            const SlabBox sb = sh.box[i & 1];
             const int b_lo = base0 + s * D;
             const int b_hi = min(b_lo + D, Nm);
             int ka = 0, kb = -1;
@@ -309,7 +317,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
             }
             __syncthreads();   // everyone is done with this buffer before it is refilled
             if (!dbl && tid == 0 && i + 1 < nsl) {
-                SlabBox sbn = slab_box(s + 1);
+                const SlabBox sbn = slab_box(s + 1);
+                sh.box[(i + 1) & 1] = sbn;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(bars[0], box_bytes);
                 tma_load_4d(smem_u32(buf0), tmap, bars[0], sbn.lo[0], sbn.lo[1], sbn.lo[2], b);
@@ -345,8 +354,9 @@ __device__ __forceinline__ void fp_tma_buffers(unsigned char *smem_raw, int buf_
     buf1 = nbuf == 2 ? (T *)(smem_raw + pad + sizeof(T) * (size_t)buf_elems) : buf0;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TMA_NT, 2) fp_tma_kernel(OpParams p, FpTmaBox cfg,
+// MINB: CTAs per SM the register allocation must allow (4 where four slab buffers fit in shared memory)
+template <typename T, int MINB>
+__global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_kernel(OpParams p, FpTmaBox cfg,
                                                            const __grid_constant__ TmaMaps maps,
                                                            const T *__restrict__ vol, T *__restrict__ sino) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -454,7 +464,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Box dimensions for the TMA kernel, or depth = 0 if it cannot be used (shared memory too small or
 // the row pitch is not a multiple of 16 bytes).
-FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf) {
+FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf, int minb) {
     FpTmaBox c{};
     const int align = 16 / (int)elem;
     if (((size_t)g->nx * elem) % 16 != 0) return c;
@@ -503,6 +513,11 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
     }
     c.buf_elems = ((maxel * (int)elem + 127) / 128) * 128 / (int)elem;
     if ((size_t)c.nbuf * c.buf_elems * elem > 200 * 1024) c.depth = 0;   // does not fit: use another kernel
+    // four CTAs per SM (registers capped at 64 per thread) where four copies of the slab buffers, the
+    // static shared memory and the per-CTA reservation fit in the SM's 228 KB; else two
+    const size_t per_cta = (size_t)c.nbuf * c.buf_elems * elem + 128 + 512 + 1024;
+    const int auto_minb = 4 * per_cta <= 228 * 1024 ? 4 : 2;
+    c.minb = minb == 2 || minb == 4 ? minb : auto_minb;
     return c;
 }
 
@@ -514,7 +529,10 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
                                    : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
     const size_t smem = (size_t)cfg.nbuf * sizeof(T) * (size_t)cfg.buf_elems + 128;
-    cudaError_t e = cudaFuncSetAttribute(fp_tma_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = cfg.minb == 4 ? fp_tma_kernel<T, 4> : fp_tma_kernel<T, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     const int nx = p.vol.nx, ny = p.vol.ny, nz = p.vol.nz;
     const int per_launch = 65535 / p.n_views > 0 ? 65535 / p.n_views : 1;
@@ -535,7 +553,7 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
             if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
         }
         dim3 grid(ceil_div(p.det.nu, TMA_TU), ceil_div(p.det.nv, TMA_TV), p.n_views * nb);
-        fp_tma_kernel<T><<<grid, TMA_NT, smem, st>>>(p, cfg, maps, vptr, (T *)sino + b0 * p.sino_elems);
+        kern<<<grid, TMA_NT, smem, st>>>(p, cfg, maps, vptr, (T *)sino + b0 * p.sino_elems);
     }
     return (int)cudaGetLastError();
 }

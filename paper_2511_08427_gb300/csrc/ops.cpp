@@ -88,7 +88,7 @@ const AdjSlabCfg &adj_cfg(pyronn_geom_t g) {
 const FpTmaBox &tma_cfg(pyronn_geom_t g, int dtype) {
     std::lock_guard<std::mutex> lk(g->mu);
     if (!g->tma_ready[dtype]) {
-        g->tma_cfg[dtype] = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf);
+        g->tma_cfg[dtype] = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf, g->tuning.fp_minb);
         g->tma_ready[dtype] = 1;
     }
     return g->tma_cfg[dtype];
@@ -165,6 +165,11 @@ int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
         case PYRONN_TUNE_FP_BUFFERS:
             if (value < 0 || value > 2) return set_error(PYRONN_INVALID_ARG, "buffer count %d out of [0, 2]", value);
             g->tuning.fp_nbuf = value;
+            break;
+        case PYRONN_TUNE_FP_CTAS_PER_SM:
+            if (value != 0 && value != 2 && value != 4)
+                return set_error(PYRONN_INVALID_ARG, "CTAs per SM must be 0 (automatic), 2 or 4 (got %d)", value);
+            g->tuning.fp_minb = value;
             break;
         case PYRONN_TUNE_ADJ_ACCUM:
             if (value < 0 || value > 2) return set_error(PYRONN_INVALID_ARG, "accumulation mode %d out of [0, 2]", value);

@@ -51,7 +51,7 @@ int pyronn_plan_create(int n, const pyronn_geom_t *geoms, int dtype, pyronn_plan
         else if ((rc = ensure_device(g)) == PYRONN_OK) {
             // volumes whose rows are not a multiple of 16 bytes (depth 0) cannot use tensor copies; the
             // forward projection runs them through the per-geometry projector on the same stream
-            FpTmaBox c = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf);
+            FpTmaBox c = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf, g->tuning.fp_minb);
             P->geoms.push_back(g);
             P->cfg.push_back(c);
         }

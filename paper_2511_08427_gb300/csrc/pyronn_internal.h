@@ -94,6 +94,7 @@ struct FpTmaBox {
     int depth, guard, slab0;   // slab depth (0: kernel unusable), guard planes, first slab plane
     int buf_elems;             // elements per buffer (max over axes)
     int nbuf;                  // 1 or 2 shared-memory buffers
+    int minb;                  // CTAs per SM the single-volume kernel is compiled for (2 or 4)
 };
 
 // Slab-ordered adjoint configuration (chosen per geometry).
@@ -128,6 +129,7 @@ struct PlanLaunch {
 struct Tuning {
     int fp_depth = 0;          // slab depth of the TMA forward projector
     int fp_nbuf = 0;           // its number of buffers
+    int fp_minb = 0;           // its CTAs per SM (2 or 4; 0 automatic)
     int adj_accum = 0;         // slab adjoint boxes: 0 automatic, 1 FP32 only, 2 fixed point with cells
 };
 
@@ -188,7 +190,7 @@ int finalize_geometry(pyronn_geom *g);          // build FP32 tables from views
 int ensure_device(pyronn_geom *g);               // upload tables to the current device
 OpParams make_params(const pyronn_geom *g, int batch);
 FpSlabCfg choose_fp_slab_cfg(const pyronn_geom *g);
-FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf);
+FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf, int minb);
 int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream);
 int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int launch_adjoint_brick_batched(const PlanLaunch &L, int dtype, int grid, void *stream);

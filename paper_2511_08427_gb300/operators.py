@@ -23,7 +23,7 @@ from ._lib import BF16, BP_INV_W2, BP_PLAIN, F16, F32, DetDesc, VolDesc, check, 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 # tuning parameters of Geometry.set_tuning (pyronn_tuning_param)
-TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM = 0, 1, 2
+TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM, TUNE_FP_CTAS_PER_SM = 0, 1, 2, 3
 
 
 def _dp(a: np.ndarray):
