@@ -507,6 +507,10 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
         // x is the innermost TMA dimension: round up, plus room for the aligned start unless the slab
         // planes themselves start aligned (march along x)
         e[0] = m == 0 ? ((e[0] + align - 1) / align) * align : ((e[0] + 2 * (align - 1)) / align) * align;
+        // march along x: all rays of a warp sit at nearly the same x, so a row pitch that is a multiple
+        // of 32 bytes would fold their rows onto 4 or fewer bank groups; an odd multiple of 16 bytes
+        // spreads consecutive rows over 8
+        if (m == 0 && (e[0] * (int)elem) % 32 == 0) e[0] += align;
         for (int a = 0; a < 3; ++a) e[a] = std::min(e[a], 256);
         c.bx[m] = e[0]; c.by[m] = e[1]; c.bz[m] = e[2];
         maxel = std::max(maxel, e[0] * e[1] * e[2]);
