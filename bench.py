@@ -37,8 +37,15 @@ WORKLOAD = dict(workload="cone-beam 256^3 circular, 360 views, 512x512 detector"
                 voxel_mm=0.5, views=360, angular_range="2pi", sid_mm=750.0, sdd_mm=1200.0, detector=[512, 512],
                 pixel_mm=0.6, phantom="20 random ellipsoids, seed 3", dt_mm=0.25)
 METRIC = "cone-beam FP G ray-samples/s and BP G voxel-view updates/s; fwd+adjoint ms/iter"
+# Algorithmic work per unit (FP32 operations counted as FLOP, an FMA as 2):
 FP_FLOP_PER_SAMPLE = 34     # 3 position FMA (6), 3 floor + 3 frac (6), 7 lerps (21), accumulate (1)
-FP_SMEM_BYTES_PER_SAMPLE = 32
+FP_SMEM_BYTES_PER_SAMPLE = 32   # eight FP32 interpolation operands
+ADJ_FLOP_PER_SAMPLE = 33    # 3 position FMA (6), 3 frac (3), 1 - a (2), z split (2), 12 weight products, 8 adds
+ADJ_RED_PER_SAMPLE = 8      # one scatter-add per trilinear corner
+BP_FLOP_PER_UPDATE = 18     # projection 3 FMA (6), reciprocal and 2 products (3), 3 bilinear lerps (6), weight, add
+# int32 shared-memory reductions per clock per SM with distinct addresses, measured on GB300 with
+# python -m paper_2511_08427_gb300.peaks (red.shared.add.u32 from every lane, 4 CTAs x 256 threads per SM)
+SMEM_RED_PER_CLK_SM = 27.28
 
 
 def _env_int(name, default):
@@ -352,15 +359,40 @@ def run_gpu(args):
     peaks, peak_src = measured_peaks()
     clk = clocks.summary()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # FP32 ALU peak from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x max SM clock
+    # FP32 ALU peak from unit counts: SMs x 128 FP32 lanes x 2 FLOP per FMA x max SM clock
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     alu_peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
-    fp_mean_s = fp_sum / K * 1e-3
-    achieved_tflops = n_samples * FP_FLOP_PER_SAMPLE / fp_mean_s / 1e12
+    alu_src = f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (unit counts, max clock)"
     smem_peak_gbs = n_sm * 128 * sm_max * 1e6 / 1e9
-    achieved_smem_gbs = n_samples * FP_SMEM_BYTES_PER_SAMPLE / fp_mean_s / 1e9
-    traffic = kernel_traffic("fp_tma_kernel", "paper_2511_08427_gb300/csrc/k_fp_tma.cu")
+    red_peak = n_sm * SMEM_RED_PER_CLK_SM * sm_max * 1e6 / 1e9
+    fp_s, adj_s, bp_s = fp_sum / K * 1e-3, adj_sum / K * 1e-3, bp_sum / K * 1e-3
+
+    def alu_roofline(kernel, source, flop, seconds):
+        achieved = flop / seconds / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": alu_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak_tflops, "traffic": kernel_traffic(kernel, source), "kernel": kernel,
+                "launch_ms": seconds * 1e3, "peak_source": alu_src}
+
+    rl_fp = alu_roofline("fp_tma_kernel", "paper_2511_08427_gb300/csrc/k_fp_tma.cu", n_samples * FP_FLOP_PER_SAMPLE, fp_s)
+    rl_fp["flop_per_sample"] = FP_FLOP_PER_SAMPLE
+    smem_gbs = n_samples * FP_SMEM_BYTES_PER_SAMPLE / fp_s / 1e9
+    rl_fp["smem"] = {"achieved_gbs": smem_gbs, "peak_gbs": smem_peak_gbs, "frac": smem_gbs / smem_peak_gbs,
+                     "bytes_per_sample": FP_SMEM_BYTES_PER_SAMPLE,
+                     "peak_source": f"{n_sm} SMs x 128 B/clk x {sm_max:.0f} MHz"}
+    rl_adj = alu_roofline("adjoint_slab_kernel", "paper_2511_08427_gb300/csrc/k_adjoint_slab.cu",
+                          n_samples * ADJ_FLOP_PER_SAMPLE, adj_s)
+    rl_adj["flop_per_sample"] = ADJ_FLOP_PER_SAMPLE
+    red_rate = n_samples * ADJ_RED_PER_SAMPLE / adj_s / 1e9
+    rl_adj["smem_reductions"] = {"achieved_gops": red_rate, "peak_gops": red_peak, "frac": red_rate / red_peak,
+                                 "per_sample": ADJ_RED_PER_SAMPLE,
+                                 "peak_source": f"{n_sm} SMs x {SMEM_RED_PER_CLK_SM} int32 red.shared/clk "
+                                                f"(measured) x {sm_max:.0f} MHz"}
+    rl_bp = alu_roofline("bp_brick_kernel", "paper_2511_08427_gb300/csrc/k_bp_brick.cu",
+                         n_updates * BP_FLOP_PER_UPDATE, bp_s)
+    rl_bp["flop_per_update"] = BP_FLOP_PER_UPDATE
+    # the dominant kernel of the step (longest average launch)
+    dominant = max((rl_fp, rl_adj, rl_bp), key=lambda r: r["launch_ms"])
 
     result = {
         "metric": METRIC, "value": fp_rate, "unit": "G ray-samples/s", "n_gpus": world, "steps": K,
@@ -376,14 +408,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(h_sino.numel() * 4), "call": "pyronn_fp_host"},
         "gpu_launches": 3 * K,
         "clocks": clk,
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / alu_peak_tflops, "traffic": traffic, "kernel": "fp_tma_kernel",
-                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (unit counts, max clock)",
-                     "flop_per_sample": FP_FLOP_PER_SAMPLE,
-                     "smem": {"achieved_gbs": achieved_smem_gbs, "peak_gbs": smem_peak_gbs,
-                              "frac": achieved_smem_gbs / smem_peak_gbs,
-                              "bytes_per_sample": FP_SMEM_BYTES_PER_SAMPLE,
-                              "peak_source": f"{n_sm} SMs x 128 B/clk x {sm_max:.0f} MHz"}},
+        "roofline": dominant,
+        "rooflines": {"fp": rl_fp, "adjoint": rl_adj, "bp": rl_bp},
     }
     result["autotune"] = {k: tuned[k] for k in ("depth", "buffers", "ms", "cached")}
     if not args.no_batched:
