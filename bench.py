@@ -43,9 +43,10 @@ FP_SMEM_BYTES_PER_SAMPLE = 32   # eight FP32 interpolation operands
 ADJ_FLOP_PER_SAMPLE = 33    # 3 position FMA (6), 3 frac (3), 1 - a (2), z split (2), 12 weight products, 8 adds
 ADJ_RED_PER_SAMPLE = 8      # one scatter-add per trilinear corner
 BP_FLOP_PER_UPDATE = 18     # projection 3 FMA (6), reciprocal and 2 products (3), 3 bilinear lerps (6), weight, add
-# int32 shared-memory reductions per clock per SM with distinct addresses, measured on GB300 with
-# python -m paper_2511_08427_gb300.peaks (red.shared.add.u32 from every lane, 4 CTAs x 256 threads per SM)
-SMEM_RED_PER_CLK_SM = 27.28
+# Shared-memory rates per clock per SM measured on GB300 (2070 MHz) with
+# python -m paper_2511_08427_gb300.peaks (every lane of 4 CTAs x 256 threads per SM, distinct banks):
+SMEM_RED_PER_CLK_SM = 28.32        # int32 red.shared.add
+SMEM_LD_BYTES_PER_CLK_SM = 4 * 27.66   # 32-bit ld.shared
 
 
 def _env_int(name, default):
@@ -364,7 +365,7 @@ def run_gpu(args):
     n_sm = props.multi_processor_count
     alu_peak_tflops = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     alu_src = f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (unit counts, max clock)"
-    smem_peak_gbs = n_sm * 128 * sm_max * 1e6 / 1e9
+    smem_peak_gbs = n_sm * SMEM_LD_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e9
     red_peak = n_sm * SMEM_RED_PER_CLK_SM * sm_max * 1e6 / 1e9
     fp_s, adj_s, bp_s = fp_sum / K * 1e-3, adj_sum / K * 1e-3, bp_sum / K * 1e-3
 
@@ -379,7 +380,8 @@ def run_gpu(args):
     smem_gbs = n_samples * FP_SMEM_BYTES_PER_SAMPLE / fp_s / 1e9
     rl_fp["smem"] = {"achieved_gbs": smem_gbs, "peak_gbs": smem_peak_gbs, "frac": smem_gbs / smem_peak_gbs,
                      "bytes_per_sample": FP_SMEM_BYTES_PER_SAMPLE,
-                     "peak_source": f"{n_sm} SMs x 128 B/clk x {sm_max:.0f} MHz"}
+                     "peak_source": f"{n_sm} SMs x {SMEM_LD_BYTES_PER_CLK_SM:.1f} B/clk (measured 32-bit "
+                                    f"ld.shared) x {sm_max:.0f} MHz"}
     rl_adj = alu_roofline("adjoint_slab_kernel", "paper_2511_08427_gb300/csrc/k_adjoint_slab.cu",
                           n_samples * ADJ_FLOP_PER_SAMPLE, adj_s)
     rl_adj["flop_per_sample"] = ADJ_FLOP_PER_SAMPLE

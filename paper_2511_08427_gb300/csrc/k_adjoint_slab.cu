@@ -289,16 +289,21 @@ __device__ __forceinline__ void as_ray_dir(const AsTile &T, float fu, float fv, 
     dd[2] = fmaf(T.dref[2], g, L2 * inv);
 }
 
+// Zeroes the box (box_cap floats); as_tile expects a zero box and leaves it zero.
+__device__ __forceinline__ void as_zero_box(float *box, int box_cap) {
+    for (int e = 4 * threadIdx.x; e + 3 < box_cap; e += 4 * AS_NT)
+        *reinterpret_cast<float4 *>(box + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = (box_cap & ~3) + threadIdx.x; e < box_cap; e += AS_NT) box[e] = 0.0f;
+}
+
+// Detector tile (tile_x, tile_y) of one view of batch item b: scatter into the FP32 volume vol.
 template <typename T>
-__global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int depth, int guard, int box_cap,
-                                                                int allow_fixed, int cell_fixed,
-                                                                const T *__restrict__ sino,
-                                                                float *__restrict__ vol) {
-    extern __shared__ __align__(16) float box[];
-    __shared__ AsShared sh;
-    const int view = blockIdx.z % p.n_views;
-    const int b = blockIdx.z / p.n_views;
-    const int tu0 = blockIdx.x * AS_TU, tv0 = blockIdx.y * AS_TV;
+__device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg, const T *__restrict__ sino,
+                                        float *__restrict__ vol, int view, int b, int tile_x, int tile_y,
+                                        float *box, AsShared &sh) {
+    const int depth = cfg.depth, guard = cfg.guard, box_cap = cfg.box_cap;
+    const int allow_fixed = cfg.allow_fixed, cell_fixed = cfg.cell_fixed;
+    const int tu0 = tile_x * AS_TU, tv0 = tile_y * AS_TV;
     const int tu1 = min(tu0 + AS_TU, p.det.nu) - 1, tv1 = min(tv0 + AS_TV, p.det.nv) - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T *sb = sino + (long long)b * p.sino_elems + (long long)view * p.det.nv * p.det.nu;
@@ -306,6 +311,7 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
     const FpRec &rec = p.fp[view];
     const float dt = p.dt;
 
+    __syncthreads();   // every thread is done with the previous tile's shared state
     // corner and centre rays (FP32, global index coordinates) for the slab boxes
     if (tid < 5) {
         float cu, cv;
@@ -393,9 +399,7 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
         atomicMin(&sh.srange[0], slo);
         atomicMax(&sh.srange[1], shi);
     }
-    // the box starts all zero; each flush zeroes what it added, so it is zero again for the next slab
-    for (int e = 4 * tid; e + 3 < box_cap; e += 4 * AS_NT) *reinterpret_cast<float4 *>(box + e) = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int e = (box_cap & ~3) + tid; e < box_cap; e += AS_NT) box[e] = 0.0f;
+    // the box is all zero on entry; each flush zeroes what it added, so it is zero again for the next slab
     __syncthreads();
     const int s_first = sh.srange[0];
     const int nsl = sh.srange[1] >= s_first ? min(sh.srange[1] - s_first + 1, AS_MAX_SLABS) : 0;
@@ -682,6 +686,43 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, int 
 }
 
 template <typename T>
+__global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, AdjSlabCfg cfg, const T *__restrict__ sino,
+                                                                float *__restrict__ vol) {
+    extern __shared__ __align__(16) float box[];
+    __shared__ AsShared sh;
+    as_zero_box(box, cfg.box_cap);
+    as_tile<T>(p, cfg, sino, vol, blockIdx.z % p.n_views, blockIdx.z / p.n_views, blockIdx.x, blockIdx.y, box, sh);
+}
+
+// Persistent launch over the (view, tile) items of several volumes (each with its own geometry and
+// slab configuration, accumulating into its own FP32 volume): each CTA takes the next item from a
+// device counter until all are done. Volumes are ordered by decreasing cost per item.
+template <typename T>
+__global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_batched_kernel(const __grid_constant__ PlanLaunch L) {
+    extern __shared__ __align__(16) float box[];
+    __shared__ AsShared sh;
+    __shared__ long long s_item;
+    int cap = 0;
+    for (int i = 0; i < L.n; ++i) cap = max(cap, L.v[i].acfg.box_cap);
+    as_zero_box(box, cap);
+    const long long total = L.item_end[L.n - 1];
+    for (;;) {
+        __syncthreads();   // every thread has read the previous item number
+        if (threadIdx.x == 0) s_item = atomicAdd(L.counter, 1);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int i = 0;
+        while (item >= L.item_end[i]) ++i;
+        const PlanVolume &V = L.v[i];
+        const long long local = item - (i ? L.item_end[i - 1] : 0);
+        const int tiles = V.ntx * V.nty;
+        const int view = (int)(local / tiles), t = (int)(local % tiles);
+        as_tile<T>(V.p, V.acfg, (const T *)V.in, V.acc, view, 0, t % V.ntx, t / V.ntx, box, sh);
+    }
+}
+
+template <typename T>
 __global__ void adjoint_convert_kernel(const float *__restrict__ src, T *__restrict__ dst, long long n) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -796,7 +837,7 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
     for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
         const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
         dim3 grid(ceil_div(p.det.nu, AS_TU), ceil_div(p.det.nv, AS_TV), p.n_views * nb);
-        adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(p, c.depth, c.guard, c.box_cap, c.allow_fixed, c.cell_fixed,
+        adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(p, c,
                                                           (const T *)sino + b0 * p.sino_elems, acc + b0 * p.vol_elems);
     }
     if ((void *)acc != vol) {
@@ -805,6 +846,48 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
         adjoint_convert_kernel<T><<<blocks, 256, 0, st>>>(acc, (T *)vol, n);
     }
     return (int)cudaGetLastError();
+}
+
+template <typename T>
+static int launch_slab_batched_t(const PlanLaunch &L, int grid, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(adjoint_slab_batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    for (int i = 0; i < L.n; ++i) {
+        e = cudaMemsetAsync(L.v[i].acc, 0, sizeof(float) * (size_t)L.v[i].p.vol_elems, st);
+        if (e != cudaSuccess) return (int)e;
+    }
+    e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return (int)e;
+    adjoint_slab_batched_kernel<T><<<grid, AS_NT, smem, st>>>(L);
+    for (int i = 0; i < L.n; ++i) {
+        if ((void *)L.v[i].acc == L.v[i].out) continue;
+        const long long n = L.v[i].p.vol_elems;
+        const int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+        adjoint_convert_kernel<T><<<blocks, 256, 0, st>>>(L.v[i].acc, (T *)L.v[i].out, n);
+    }
+    return (int)cudaGetLastError();
+}
+
+// One persistent slab-ordered adjoint launch over a plan's volumes (each PlanVolume carries its slab
+// configuration and FP32 accumulation volume, which is zeroed here; other element types are converted
+// into the output afterwards). smem: the largest box of the plan, in bytes.
+int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_slab_batched_t<float>(L, grid, smem, st);
+        case PYRONN_BF16: return launch_slab_batched_t<__nv_bfloat16>(L, grid, smem, st);
+        case PYRONN_F16: return launch_slab_batched_t<__half>(L, grid, smem, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int adjoint_slab_batched_occupancy(size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(adjoint_slab_batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adjoint_slab_batched_kernel<float>, AS_NT,
+                                                              smem);
 }
 
 int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino, void *vol, float *acc32, int dtype,

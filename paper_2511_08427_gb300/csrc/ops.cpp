@@ -8,6 +8,19 @@
 
 using namespace pyronn;
 
+namespace pyronn {
+
+const AdjSlabCfg &geom_adj_cfg(pyronn_geom *g) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (!g->adj_cfg_ready) {
+        g->adj_cfg = choose_adj_slab_cfg(g);
+        g->adj_cfg_ready = 1;
+    }
+    return g->adj_cfg;
+}
+
+}  // namespace pyronn
+
 namespace {
 
 int check_ptr(const void *p, const char *what) {
@@ -76,14 +89,7 @@ const FpSlabCfg &fp_cfg(pyronn_geom_t g) {
     return g->fp_cfg;
 }
 
-const AdjSlabCfg &adj_cfg(pyronn_geom_t g) {
-    std::lock_guard<std::mutex> lk(g->mu);
-    if (!g->adj_cfg_ready) {
-        g->adj_cfg = choose_adj_slab_cfg(g);
-        g->adj_cfg_ready = 1;
-    }
-    return g->adj_cfg;
-}
+const AdjSlabCfg &adj_cfg(pyronn_geom_t g) { return geom_adj_cfg(g); }
 
 const FpTmaBox &tma_cfg(pyronn_geom_t g, int dtype) {
     std::lock_guard<std::mutex> lk(g->mu);

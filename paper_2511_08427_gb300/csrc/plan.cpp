@@ -21,6 +21,13 @@ struct pyronn_plan {
     int *d_counter = nullptr;           // three counters: FP, adjoint, BP
     int fp_grid = 0, adj_grid = 0, bp_grid = 0;
     size_t fp_smem = 0;
+    // adjoint: slab-ordered (persistent, shared-memory boxes) where every geometry has a slab
+    // configuration, else output-stationary bricks
+    bool adj_slab = false;
+    size_t adj_smem = 0;
+    std::vector<AdjSlabCfg> acfg;
+    float *d_acc = nullptr;             // FP32 accumulation volumes (BF16 / FP16 plans)
+    std::vector<size_t> acc_off;
 };
 
 namespace {
@@ -108,8 +115,34 @@ int pyronn_plan_create(int n, const pyronn_geom_t *geoms, int dtype, pyronn_plan
         return cuda_err(e, "back-projector occupancy");
     }
     P->bp_grid = sms * std::max(occ, 1);
+    // slab-ordered adjoint for the whole plan if every geometry has a valid slab configuration
+    P->adj_slab = true;
+    size_t acc_total = 0;
+    for (int i = 0; i < n; ++i) {
+        const AdjSlabCfg &c = geom_adj_cfg(P->geoms[i]);
+        P->acfg.push_back(c);
+        P->acc_off.push_back(acc_total);
+        acc_total += (size_t)P->geoms[i]->nx * P->geoms[i]->ny * P->geoms[i]->nz;
+        if (!c.valid || (P->geoms[i]->adj_variant != 0 && P->geoms[i]->adj_variant != 3)) P->adj_slab = false;
+        P->adj_smem = std::max(P->adj_smem, sizeof(float) * (size_t)c.box_cap);
+    }
+    if (P->adj_slab) {
+        if ((e = (cudaError_t)adjoint_slab_batched_occupancy(P->adj_smem, &occ)) != cudaSuccess) {
+            delete P;
+            return cuda_err(e, "slab adjoint occupancy");
+        }
+        P->adj_grid = sms * std::max(occ, 1);
+        if (dtype != PYRONN_F32) {
+            e = cudaMalloc(&P->d_acc, sizeof(float) * acc_total);
+            if (e != cudaSuccess) {
+                delete P;
+                return set_error(PYRONN_OOM, "adjoint accumulation volumes: %s", cudaGetErrorString(e));
+            }
+        }
+    }
     e = cudaMalloc(&P->d_counter, 4 * sizeof(int));
     if (e != cudaSuccess) {
+        if (P->d_acc) cudaFree(P->d_acc);
         delete P;
         return set_error(PYRONN_OOM, "work counters: %s", cudaGetErrorString(e));
     }
@@ -121,6 +154,7 @@ int pyronn_plan_destroy(pyronn_plan_t P) {
     clear_error();
     if (!P) return PYRONN_OK;
     if (P->d_counter) cudaFree(P->d_counter);
+    if (P->d_acc) cudaFree(P->d_acc);
     delete P;
     return PYRONN_OK;
 }
@@ -224,7 +258,32 @@ static int brick_launch(pyronn_plan_t P, const void *const *sinos, void *const *
 }
 
 int pyronn_plan_adjoint(pyronn_plan_t P, const void *const *sinos, void *const *vols, void *stream) {
-    return brick_launch(P, sinos, vols, PYRONN_BP_PLAIN, stream, 1);
+    if (!P || !P->adj_slab) return brick_launch(P, sinos, vols, PYRONN_BP_PLAIN, stream, 1);
+    clear_error();
+    int rc = check_ptrs(P, sinos, (const void *const *)vols);
+    if (rc) return rc;
+    // items (view, 32 x 32 detector tile), volumes with the longest rays first
+    PlanLaunch L{};
+    L.n = P->n;
+    L.counter = P->d_counter + 1;
+    long long acc = 0;
+    for (int k = 0; k < P->n; ++k) {
+        const int i = P->order_fp[k];
+        pyronn_geom *g = P->geoms[i];
+        PlanVolume &V = L.v[k];
+        V.p = make_params(g, 1);
+        V.acfg = P->acfg[i];
+        V.in = sinos[i];
+        V.out = vols[i];
+        V.acc = P->dtype == PYRONN_F32 ? (float *)vols[i] : P->d_acc + P->acc_off[i];
+        V.ntx = (g->nu + 31) / 32;
+        V.nty = (g->nv + 31) / 32;
+        V.ntz = 1;
+        acc += (long long)g->n_views * V.ntx * V.nty;
+        L.item_end[k] = acc;
+    }
+    const int e = launch_adjoint_slab_batched(L, P->dtype, P->adj_grid, P->adj_smem, stream);
+    return e ? cuda_err((cudaError_t)e, "batched adjoint") : PYRONN_OK;
 }
 
 int pyronn_plan_bp(pyronn_plan_t P, const void *const *sinos, void *const *vols, int weight, void *stream) {

@@ -116,6 +116,8 @@ struct PlanVolume {
     int ntx, nty;              // work tiles: detector tiles (FP) or volume bricks in x, y (adjoint, BP)
     int ntz;                   // bricks in z (adjoint, BP)
     int per_item;              // views per item group: FP items are (view, tile)
+    AdjSlabCfg acfg;           // slab-ordered adjoint: slab configuration of this geometry
+    float *acc;                // slab-ordered adjoint: FP32 accumulation volume (the output for FP32)
 };
 struct PlanLaunch {
     int n;
@@ -194,6 +196,9 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
 int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream);
 int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int launch_adjoint_brick_batched(const PlanLaunch &L, int dtype, int grid, void *stream);
+int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
+int adjoint_slab_batched_occupancy(size_t smem, int *blocks_per_sm);
+const AdjSlabCfg &geom_adj_cfg(pyronn_geom *g);   // cached per geometry (host computation)
 int adjoint_brick_batched_occupancy(int *blocks_per_sm);
 int launch_bp_brick_batched(const PlanLaunch &L, int dtype, int weight, int grid, void *stream);
 int bp_brick_batched_occupancy(int *blocks_per_sm);

@@ -73,8 +73,8 @@ def test_plan_matches_single_operators_and_oracle(ops):
         ref_fp = ops.forward_project(xs[i], g)
         assert rel_l2(host(sinos[i]), host(ref_fp)) <= 1e-6, i
         assert rel_l2(host(sinos[i]), oracle.fp(og, vols[i])) <= 1e-5, i
-        # the plan's adjoint (bricks) and the default single-geometry adjoint (slabs) are different
-        # summation orders of the same operator: both within the oracle tolerance
+        # the plan's persistent slab adjoint and the single-geometry launch add the boxes to the volume
+        # in different orders: both within the oracle tolerance
         assert rel_l2(host(adj[i]), host(ops.adjoint(ys[i], g))) <= 1e-5, i
         assert rel_l2(host(adj[i]), oracle.adjoint(og, host(ys[i]))) <= 1e-5, i
         assert rel_l2(host(bps[i]), host(ops.back_project(ys[i], g, 1))) <= 1e-6, i
