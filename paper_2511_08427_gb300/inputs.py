@@ -160,6 +160,21 @@ def poisson_log_sinogram(p: np.ndarray, i0: float, seed: int, scale_to_max: floa
     return (-np.log(np.maximum(c, 1.0) / i0)).astype(np.float32)
 
 
+def poisson_log_sinogram_torch(p, i0: float, seed: int, scale_to_max: float | None = 3.0):
+    """The photon-noise recipe of poisson_log_sinogram on a torch tensor (for sinograms too large for the
+    host): same model and clamping, counts drawn by torch.poisson with a generator seeded by seed on the
+    tensor's device. Returns FP32 noisy line integrals."""
+    import torch
+    gen = torch.Generator(device=p.device).manual_seed(seed)
+    p = p.float()
+    if scale_to_max is not None:
+        pmax = p.max()
+        if pmax > 0:
+            p = p * (scale_to_max / pmax)
+    c = torch.poisson(i0 * torch.exp(-p), generator=gen)
+    return -torch.log(torch.clamp(c, min=1.0) / i0)
+
+
 @dataclass
 class Trajectory:
     """Per-view source position, detector centre and detector axes, world mm (float64, V x 3 each)."""
