@@ -375,8 +375,8 @@ struct PlanMaps {
     CUtensorMap map[PLAN_MAX][3];
 };
 
-template <typename T>
-__global__ void __launch_bounds__(TMA_NT, 2) fp_tma_batched_kernel(const __grid_constant__ PlanLaunch L,
+template <typename T, int MINB>
+__global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_batched_kernel(const __grid_constant__ PlanLaunch L,
                                                                    const __grid_constant__ PlanMaps M) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ FpTmaShared sh;
@@ -584,10 +584,15 @@ static int encode_maps(const OpParams &p, const FpTmaBox &cfg, const void *vol, 
     return 0;
 }
 
+// the persistent kernel is compiled for four CTAs per SM (64 registers) where four CTAs' buffers fit
+static bool batched_four(size_t smem) { return 4 * (smem + 512 + 1024) <= 228 * 1024; }
+
 template <typename T>
 static int launch_batched_t(const PlanLaunch &L, int grid, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(fp_tma_batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = batched_four(smem) ? fp_tma_batched_kernel<T, 4> : fp_tma_batched_kernel<T, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     PlanMaps M;
     std::memset(&M, 0, sizeof(M));
@@ -597,7 +602,7 @@ static int launch_batched_t(const PlanLaunch &L, int grid, size_t smem, cudaStre
     }
     e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return (int)e;
-    fp_tma_batched_kernel<T><<<grid, TMA_NT, smem, st>>>(L, M);
+    kern<<<grid, TMA_NT, smem, st>>>(L, M);
     return (int)cudaGetLastError();
 }
 
@@ -611,29 +616,23 @@ int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem,
     }
 }
 
+template <typename T>
+static int batched_occupancy_t(size_t smem, int *blocks_per_sm) {
+    auto kern = batched_four(smem) ? fp_tma_batched_kernel<T, 4> : fp_tma_batched_kernel<T, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, TMA_NT, smem);
+    return (int)e;
+}
+
 int fp_tma_batched_occupancy(int dtype, size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaSuccess;
     switch (dtype) {
-        case PYRONN_F32:
-            e = cudaFuncSetAttribute(fp_tma_batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fp_tma_batched_kernel<float>, TMA_NT, smem);
-            break;
-        case PYRONN_BF16:
-            e = cudaFuncSetAttribute(fp_tma_batched_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fp_tma_batched_kernel<__nv_bfloat16>,
-                                                                  TMA_NT, smem);
-            break;
-        case PYRONN_F16:
-            e = cudaFuncSetAttribute(fp_tma_batched_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fp_tma_batched_kernel<__half>, TMA_NT, smem);
-            break;
+        case PYRONN_F32: return batched_occupancy_t<float>(smem, blocks_per_sm);
+        case PYRONN_BF16: return batched_occupancy_t<__nv_bfloat16>(smem, blocks_per_sm);
+        case PYRONN_F16: return batched_occupancy_t<__half>(smem, blocks_per_sm);
         default: return (int)cudaErrorInvalidValue;
     }
-    return (int)e;
 }
 
 int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream) {
