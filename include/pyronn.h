@@ -162,6 +162,16 @@ PYRONN_API int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype
  * geometry-owned scratch buffer (allocated on first use) and converted once at the end. */
 PYRONN_API int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, void *stream);
 
+/* Fused gradient step (the data-term update of an iterative reconstruction, Sec. 2.2 "known operator"
+ * networks; no dedicated passage in the paper): vol += alpha * A^T (sino - sino_b), accumulating into
+ * vol in place. sino_b may be NULL (then vol += alpha A^T sino). With the slab-ordered adjoint the
+ * residual is formed while the sinogram is read and the sum is added straight into vol (FP32), or into
+ * an FP32 copy of vol that is converted back (BF16 / FP16); other adjoint kernels go through
+ * geometry-owned work buffers (a residual sinogram and an adjoint volume, allocated on first use).
+ * Same layouts, alignment and error behaviour as pyronn_adjoint; alpha must be finite. */
+PYRONN_API int pyronn_adjoint_update(pyronn_geom_t g, const void *sino, const void *sino_b, double alpha, void *vol,
+                                     int dtype, int batch, void *stream);
+
 /* Voxel-driven back-projection (Sec. 2.1): vol = BP sino, overwriting vol; weight is a
  * pyronn_bp_weight. Not the transpose of pyronn_fp. */
 PYRONN_API int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, int weight, void *stream);

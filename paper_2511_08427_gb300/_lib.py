@@ -57,6 +57,7 @@ SIGNATURES = [
     ("pyronn_geom_set_tuning", _c_int, [_vp, _c_int, _c_int]),
     ("pyronn_fp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_adjoint", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
+    ("pyronn_adjoint_update", _c_int, [_vp, _vp, _vp, ctypes.c_double, _vp, _c_int, _c_int, _vp]),
     ("pyronn_bp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_bp_transpose", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_adjoint_noalloc", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),

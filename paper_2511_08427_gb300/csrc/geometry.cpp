@@ -504,7 +504,7 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
     clear_error();
     if (!g) return PYRONN_OK;
     // device buffers are freed on the device they were allocated on
-    if (g->d_fp || g->d_scratch || g->d_stage_in || g->d_stage_out) {
+    if (g->d_fp || g->d_scratch || g->d_stage_in || g->d_stage_out || g->d_upd_sino || g->d_upd_vol) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (g->device >= 0 && g->device != cur) cudaSetDevice(g->device);
@@ -515,6 +515,8 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
         cudaFree(g->d_scratch);
         cudaFree(g->d_stage_in);
         cudaFree(g->d_stage_out);
+        cudaFree(g->d_upd_sino);
+        cudaFree(g->d_upd_vol);
         if (g->device >= 0 && cur >= 0 && g->device != cur) cudaSetDevice(cur);
     }
     delete g;

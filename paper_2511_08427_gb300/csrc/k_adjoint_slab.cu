@@ -296,17 +296,20 @@ __device__ __forceinline__ void as_zero_box(float *box, int box_cap) {
     for (int e = (box_cap & ~3) + threadIdx.x; e < box_cap; e += AS_NT) box[e] = 0.0f;
 }
 
-// Detector tile (tile_x, tile_y) of one view of batch item b: scatter into the FP32 volume vol.
+// Detector tile (tile_x, tile_y) of one view of batch item b: adds y_scale A^T (sino - sino_b) (sino_b
+// may be null) into the FP32 volume vol.
 template <typename T>
 __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg, const T *__restrict__ sino,
-                                        float *__restrict__ vol, int view, int b, int tile_x, int tile_y,
-                                        float *box, AsShared &sh) {
+                                        const T *__restrict__ sino_b, float y_scale, float *__restrict__ vol,
+                                        int view, int b, int tile_x, int tile_y, float *box, AsShared &sh) {
     const int depth = cfg.depth, guard = cfg.guard, box_cap = cfg.box_cap;
     const int allow_fixed = cfg.allow_fixed, cell_fixed = cfg.cell_fixed;
     const int tu0 = tile_x * AS_TU, tv0 = tile_y * AS_TV;
     const int tu1 = min(tu0 + AS_TU, p.det.nu) - 1, tv1 = min(tv0 + AS_TV, p.det.nv) - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const T *sb = sino + (long long)b * p.sino_elems + (long long)view * p.det.nv * p.det.nu;
+    const long long s_off = (long long)b * p.sino_elems + (long long)view * p.det.nv * p.det.nu;
+    const T *sb = sino + s_off;
+    const T *sb2 = sino_b ? sino_b + s_off : nullptr;
     float *vb = vol + (long long)b * p.vol_elems;
     const FpRec &rec = p.fp[view];
     const float dt = p.dt;
@@ -357,7 +360,13 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
 #pragma unroll
     for (int j = 0; j < AS_RPT; ++j) {
         const int u = tu0 + lane, v = tv0 + warp * AS_RPT + j;
-        yv[j] = (u <= tu1 && v <= tv1) ? ldg_f32(sb + (long long)v * p.det.nu + u) * dt : 0.0f;
+        float yj = 0.0f;
+        if (u <= tu1 && v <= tv1) {
+            const long long o = (long long)v * p.det.nu + u;
+            yj = ldg_f32(sb + o);
+            if (sb2) yj -= ldg_f32(sb2 + o);   // fused residual of a gradient step
+        }
+        yv[j] = yj * (dt * y_scale);
         ybits = max(ybits, __float_as_uint(fabsf(yv[j])));
         rcm[j] = 0.0f;
         rinv[j] = 0.0f;
@@ -687,11 +696,13 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
 
 template <typename T>
 __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, AdjSlabCfg cfg, const T *__restrict__ sino,
+                                                                const T *__restrict__ sino_b, float y_scale,
                                                                 float *__restrict__ vol) {
     extern __shared__ __align__(16) float box[];
     __shared__ AsShared sh;
     as_zero_box(box, cfg.box_cap);
-    as_tile<T>(p, cfg, sino, vol, blockIdx.z % p.n_views, blockIdx.z / p.n_views, blockIdx.x, blockIdx.y, box, sh);
+    as_tile<T>(p, cfg, sino, sino_b, y_scale, vol, blockIdx.z % p.n_views, blockIdx.z / p.n_views, blockIdx.x,
+               blockIdx.y, box, sh);
 }
 
 // Persistent launch over the (view, tile) items of several volumes (each with its own geometry and
@@ -718,7 +729,8 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_batched_kernel(const __
         const long long local = item - (i ? L.item_end[i - 1] : 0);
         const int tiles = V.ntx * V.nty;
         const int view = (int)(local / tiles), t = (int)(local % tiles);
-        as_tile<T>(V.p, V.acfg, (const T *)V.in, V.acc, view, 0, t % V.ntx, t / V.ntx, box, sh);
+        as_tile<T>(V.p, V.acfg, (const T *)V.in, (const T *)nullptr, 1.0f, V.acc, view, 0, t % V.ntx, t / V.ntx,
+                   box, sh);
     }
 }
 
@@ -826,9 +838,23 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
 }
 
 template <typename T>
-static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sino, float *acc, void *vol,
-                         cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)p.vol_elems * p.batch, st);
+__global__ void adjoint_widen_kernel(const T *__restrict__ src, float *__restrict__ dst, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) dst[i] = to_f32<T>(src[i]);
+}
+
+// vol = y_scale A^T (sino - sino_b), or vol += ... when accumulate (sino_b may be null). acc: the FP32
+// accumulation volume (vol itself for FP32; for BF16 / FP16 it is widened from vol first when
+// accumulating and converted back at the end).
+template <typename T>
+static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sino, const void *sino_b, float y_scale,
+                         bool accumulate, float *acc, void *vol, cudaStream_t st) {
+    const long long n = p.vol_elems * p.batch;
+    const int cblocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    cudaError_t e = cudaSuccess;
+    if (!accumulate) e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)n, st);
+    else if ((void *)acc != vol) adjoint_widen_kernel<T><<<cblocks, 256, 0, st>>>((const T *)vol, acc, n);
     if (e != cudaSuccess) return (int)e;
     const size_t smem = sizeof(float) * (size_t)c.box_cap;
     e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -837,14 +863,11 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
     for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
         const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
         dim3 grid(ceil_div(p.det.nu, AS_TU), ceil_div(p.det.nv, AS_TV), p.n_views * nb);
-        adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(p, c,
-                                                          (const T *)sino + b0 * p.sino_elems, acc + b0 * p.vol_elems);
+        adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(
+            p, c, (const T *)sino + b0 * p.sino_elems,
+            sino_b ? (const T *)sino_b + b0 * p.sino_elems : (const T *)nullptr, y_scale, acc + b0 * p.vol_elems);
     }
-    if ((void *)acc != vol) {
-        const long long n = p.vol_elems * p.batch;
-        const int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
-        adjoint_convert_kernel<T><<<blocks, 256, 0, st>>>(acc, (T *)vol, n);
-    }
+    if ((void *)acc != vol) adjoint_convert_kernel<T><<<cblocks, 256, 0, st>>>(acc, (T *)vol, n);
     return (int)cudaGetLastError();
 }
 
@@ -890,13 +913,14 @@ int adjoint_slab_batched_occupancy(size_t smem, int *blocks_per_sm) {
                                                               smem);
 }
 
-int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino, void *vol, float *acc32, int dtype,
-                        void *stream) {
+int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino, const void *sino_b, float y_scale,
+                        bool accumulate, void *vol, float *acc32, int dtype, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     switch (dtype) {
-        case PYRONN_F32: return launch_slab_t<float>(p, c, sino, (float *)vol, vol, st);
-        case PYRONN_BF16: return launch_slab_t<__nv_bfloat16>(p, c, sino, acc32, vol, st);
-        case PYRONN_F16: return launch_slab_t<__half>(p, c, sino, acc32, vol, st);
+        case PYRONN_F32: return launch_slab_t<float>(p, c, sino, sino_b, y_scale, accumulate, (float *)vol, vol, st);
+        case PYRONN_BF16:
+            return launch_slab_t<__nv_bfloat16>(p, c, sino, sino_b, y_scale, accumulate, acc32, vol, st);
+        case PYRONN_F16: return launch_slab_t<__half>(p, c, sino, sino_b, y_scale, accumulate, acc32, vol, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -1,6 +1,7 @@
 // C ABI of the operators: argument validation, lazy device set-up and dispatch to the kernels.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 
@@ -55,6 +56,19 @@ int ensure_scratch(pyronn_geom_t g, size_t bytes) {
     cudaError_t e = cudaMalloc(&g->d_scratch, bytes);
     if (e != cudaSuccess) return set_error(PYRONN_OOM, "scratch allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
     g->scratch_bytes = bytes;
+    return PYRONN_OK;
+}
+
+// Grows a geometry-owned device buffer to at least `bytes`.
+int ensure_buffer(pyronn_geom_t g, void **buf, size_t *cur, size_t bytes, const char *what) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (*cur >= bytes) return PYRONN_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cur = 0;
+    cudaError_t e = cudaMalloc(buf, bytes);
+    if (e != cudaSuccess) return set_error(PYRONN_OOM, "%s allocation of %zu bytes: %s", what, bytes, cudaGetErrorString(e));
+    *cur = bytes;
     return PYRONN_OK;
 }
 
@@ -214,7 +228,8 @@ int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int dtype, int 
                 if ((rc = ensure_scratch(g, sizeof(float) * (size_t)p.vol_elems * batch))) return rc;
                 acc = (float *)g->d_scratch;
             }
-            return cuda_rc(launch_adjoint_slab(p, ac, sino, vol, acc, dtype, stream), "adjoint launch");
+            return cuda_rc(launch_adjoint_slab(p, ac, sino, nullptr, 1.0f, false, vol, acc, dtype, stream),
+                           "adjoint launch");
         }
     }
     if (g->adj_variant != 1) return cuda_rc(launch_adjoint_brick(p, sino, vol, dtype, stream), "adjoint launch");
@@ -224,6 +239,41 @@ int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int dtype, int 
         acc = (float *)g->d_scratch;
     }
     return cuda_rc(launch_adjoint(p, sino, vol, acc, dtype, stream), "adjoint launch");
+}
+
+int pyronn_adjoint_update(pyronn_geom_t g, const void *sino, const void *sino_b, double alpha, void *vol, int dtype,
+                          int batch, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
+    if (sino_b && (rc = check_ptr(sino_b, "sino_b"))) return rc;
+    if (!std::isfinite(alpha)) return set_error(PYRONN_INVALID_ARG, "alpha must be finite");
+    OpParams p = make_params(g, batch);
+    if (g->adj_variant == 0 || g->adj_variant == 3) {
+        const AdjSlabCfg &ac = adj_cfg(g);
+        if (ac.valid) {
+            float *acc = nullptr;
+            if (dtype != PYRONN_F32) {
+                if ((rc = ensure_scratch(g, sizeof(float) * (size_t)p.vol_elems * batch))) return rc;
+                acc = (float *)g->d_scratch;
+            }
+            return cuda_rc(launch_adjoint_slab(p, ac, sino, sino_b, (float)alpha, true, vol, acc, dtype, stream),
+                           "adjoint update launch");
+        }
+    }
+    // kernels without the fused form: residual into a work sinogram, adjoint into a work volume, axpy
+    const size_t es = dtype_size(dtype);
+    const long long ns = p.sino_elems * batch, nv = p.vol_elems * batch;
+    const void *y = sino;
+    if (sino_b) {
+        if ((rc = ensure_buffer(g, &g->d_upd_sino, &g->upd_sino_bytes, es * (size_t)ns, "update sinogram"))) return rc;
+        if ((rc = cuda_rc(launch_residual(sino, sino_b, g->d_upd_sino, ns, dtype, stream), "residual launch"))) return rc;
+        y = g->d_upd_sino;
+    }
+    if ((rc = ensure_buffer(g, &g->d_upd_vol, &g->upd_vol_bytes, es * (size_t)nv, "update volume"))) return rc;
+    if ((rc = pyronn_adjoint(g, y, g->d_upd_vol, dtype, batch, stream))) return rc;
+    return cuda_rc(launch_axpy(vol, g->d_upd_vol, (float)alpha, nv, dtype, stream), "update launch");
 }
 
 int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, int weight, void *stream) {

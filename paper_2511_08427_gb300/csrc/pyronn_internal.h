@@ -164,6 +164,9 @@ struct pyronn_geom {
     double *d_views64 = nullptr;
     void *d_scratch = nullptr;     // FP32 accumulation buffer for reduced-precision adjoints
     size_t scratch_bytes = 0;
+    void *d_upd_sino = nullptr;    // work buffers of pyronn_adjoint_update on the unfused kernels
+    void *d_upd_vol = nullptr;
+    size_t upd_sino_bytes = 0, upd_vol_bytes = 0;
     void *d_stage_in = nullptr;    // device buffers of the host-buffer entry points
     void *d_stage_out = nullptr;
     size_t stage_in_bytes = 0, stage_out_bytes = 0;
@@ -196,6 +199,8 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
 int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream);
 int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int launch_adjoint_brick_batched(const PlanLaunch &L, int dtype, int grid, void *stream);
+int launch_residual(const void *a, const void *b, void *out, long long n, int dtype, void *stream);
+int launch_axpy(void *vol, const void *w, float alpha, long long n, int dtype, void *stream);
 int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int adjoint_slab_batched_occupancy(size_t smem, int *blocks_per_sm);
 const AdjSlabCfg &geom_adj_cfg(pyronn_geom *g);   // cached per geometry (host computation)
@@ -210,8 +215,8 @@ int launch_fp_direct(const OpParams &p, const void *vol, void *sino, int dtype, 
 int launch_adjoint(const OpParams &p, const void *sino, void *vol, float *acc32, int dtype, void *stream);
 int launch_adjoint_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g);
-int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino, void *vol, float *acc32, int dtype,
-                        void *stream);
+int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino, const void *sino_b, float y_scale,
+                        bool accumulate, void *vol, float *acc32, int dtype, void *stream);
 int launch_adjoint_scatter_acc(const OpParams &p, const void *sino, float *acc, void *vol, int dtype, void *stream);
 int launch_bp(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);

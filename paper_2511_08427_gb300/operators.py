@@ -252,6 +252,31 @@ def adjoint(sino: torch.Tensor, g: Geometry, out: torch.Tensor | None = None) ->
     return out
 
 
+def adjoint_update(vol: torch.Tensor, sino: torch.Tensor, g: Geometry, alpha: float,
+                   sino_b: torch.Tensor | None = None) -> torch.Tensor:
+    """vol += alpha A^T (sino - sino_b) in place (sino_b optional): the fused data-term update of a
+    gradient step (pyronn_adjoint_update). Returns vol."""
+    dt = _check(sino, "sinogram")
+    if vol.dtype != sino.dtype or (sino_b is not None and sino_b.dtype != sino.dtype):
+        raise TypeError("volume and sinograms must share one element type")
+    if not vol.is_contiguous():
+        raise ValueError("the updated volume must be contiguous")
+    sino = sino.contiguous()
+    lead, nb = _batch(sino, _sino_dims(g), "sinogram")
+    if tuple(vol.shape) != lead + _vol_dims(g):
+        raise ValueError(f"volume shape {tuple(vol.shape)} does not match {lead + _vol_dims(g)}")
+    sb = 0
+    if sino_b is not None:
+        sino_b = sino_b.contiguous()
+        if sino_b.shape != sino.shape:
+            raise ValueError("sino_b must have the shape of sino")
+        sb = sino_b.data_ptr()
+    with torch.cuda.device(sino.device):
+        check(lib().pyronn_adjoint_update(g.handle, sino.data_ptr(), sb, float(alpha), vol.data_ptr(), dt, nb,
+                                          _stream_ptr(sino.device)))
+    return vol
+
+
 def back_project(sino: torch.Tensor, g: Geometry, weight: int = BP_PLAIN, out: torch.Tensor | None = None):
     """vol = BP sino (voxel-driven back-projection, Sec. 2.1); weight BP_PLAIN or BP_INV_W2."""
     dt = _check(sino, "sinogram")
@@ -383,6 +408,40 @@ class BackProjectFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad):
         return back_project_transpose(grad.contiguous(), ctx.g, ctx.weight), None, None
+
+
+class GradientStepFn(torch.autograd.Function):
+    """x_next = x - alpha A^T (A x - p) with the fused update kernel (one projection, one fused adjoint).
+    Backward: grad_x = g - alpha A^T A g (fused again), grad_p = alpha A g,
+    grad_alpha = -<A g, A x - p>."""
+
+    @staticmethod
+    def forward(ctx, x, p, alpha, g):
+        pm = forward_project(x.contiguous(), g)
+        a = float(alpha)
+        out = adjoint_update(x.detach().clone(memory_format=torch.contiguous_format), pm, g, -a, sino_b=p)
+        ctx.g = g
+        ctx.alpha = a
+        ctx.save_for_backward(pm, p, alpha)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad):
+        pm, p, alpha = ctx.saved_tensors
+        g, a = ctx.g, ctx.alpha
+        grad = grad.contiguous()
+        ag = forward_project(grad, g)
+        gx = adjoint_update(grad.clone(), ag, g, -a) if ctx.needs_input_grad[0] else None
+        gp = a * ag if ctx.needs_input_grad[1] else None
+        galpha = None
+        if ctx.needs_input_grad[2]:
+            galpha = (-torch.sum(ag * (pm - p), dtype=torch.float64)).to(alpha.dtype).reshape(alpha.shape)
+        return gx, gp, galpha, None
+
+
+def gradient_step(x, p, alpha, g):
+    """x - alpha A^T (A x - p) (fused update, differentiable in x, p and alpha)."""
+    return GradientStepFn.apply(x, p, alpha, g)
 
 
 def project(vol, g):

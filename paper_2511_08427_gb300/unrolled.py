@@ -9,7 +9,10 @@ alpha_k are trainable (initialised to 1 / (max(A 1) max(A^T 1)), which is at mos
 term 0.5 ||A x - p||^2 decreases at every step). Gradients reach the alphas and p through the
 autograd functions of `operators` (backward of A = A^T, of A^T = A). With checkpoint=True each
 iteration is recomputed in the backward pass instead of storing its intermediate sinogram and
-volume (torch.utils.checkpoint), so memory stays at one iterate per step.
+volume (torch.utils.checkpoint), so memory stays at one iterate per step. With fused=True every
+iteration is one projection and one fused adjoint update (operators.gradient_step: the residual is
+formed while the adjoint reads the sinogram and the update accumulates into the iterate), and so is
+its backward.
 """
 from __future__ import annotations
 
@@ -35,15 +38,18 @@ class UnrolledGD(torch.nn.Module):
     """K gradient-descent steps on 0.5 ||A x - p||^2 with one trainable step size per iteration."""
 
     def __init__(self, g: ops.Geometry, iterations: int = 10, alpha0: float | None = None, checkpoint: bool = True,
-                 device=None):
+                 device=None, fused: bool = True):
         super().__init__()
         self.g = g
         self.iterations = int(iterations)
         self.checkpoint = bool(checkpoint)
+        self.fused = bool(fused)
         a = step_bound(g, device) if alpha0 is None else float(alpha0)
         self.alpha = torch.nn.Parameter(torch.full((self.iterations,), a, device=device or torch.device("cuda")))
 
     def _step(self, x: torch.Tensor, p: torch.Tensor, k: int) -> torch.Tensor:
+        if self.fused:
+            return ops.gradient_step(x, p, self.alpha[k], self.g)
         r = ops.project(x, self.g) - p
         return x - self.alpha[k] * ops.project_adjoint(r, self.g)
 

@@ -159,3 +159,84 @@ def test_unrolled_gd_checkpoint_matches_stored_and_finite_difference(ops):
     am[k] -= h
     fd = (loss(ap) - loss(am)) / (2 * h)
     assert abs(fd - float(grads[1][k])) <= 2e-3 * abs(float(grads[1][k])) + 1e-9
+
+
+@pytest.mark.parametrize("name", ["cone", "jittered_positions", "fan2d"])
+@pytest.mark.parametrize("with_b", [True, False])
+def test_adjoint_update_matches_composition_and_oracle(ops, name, with_b):
+    """vol += alpha A^T (a - b): fused (3D: slab adjoint) or through work buffers (2D), against the
+    unfused composition and the oracle."""
+    from cases import SMALL
+    case = next(c for c in SMALL if c.name == name)
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    sshape = (og.n_views, -1) if case.ndim == 2 else og.sino_shape
+    a = inputs.gaussian(og.sino_shape, seed=50)
+    b = inputs.gaussian(og.sino_shape, seed=51) if with_b else np.zeros(og.sino_shape, np.float32)
+    v0 = inputs.gaussian(og.vol_shape, seed=52).reshape(case.params["vol_shape"] if case.ndim == 2 else og.vol_shape)
+    alpha = -0.37
+    vol = torch.from_numpy(v0).to(DEV)
+    ad = torch.from_numpy(a.reshape(sshape)).to(DEV)
+    bd = torch.from_numpy(b.reshape(sshape)).to(DEV) if with_b else None
+    ops.adjoint_update(vol, ad, g, alpha, sino_b=bd)
+    ref = torch.from_numpy(v0).to(DEV) + alpha * ops.adjoint(ad - bd if with_b else ad, g)
+    assert rel_l2(host(vol), host(ref)) <= 1e-6
+    ora = v0.astype(np.float64).ravel() + alpha * oracle.adjoint(og, (a.astype(np.float64) - b)).ravel()
+    assert rel_l2(host(vol).ravel(), ora) <= 1e-5
+
+
+def test_adjoint_update_bf16(ops):
+    from cases import SMALL
+    case = next(c for c in SMALL if c.name == "cone")
+    g = case.library_geometry()
+    og = case.oracle_geometry()
+    a = torch.from_numpy(inputs.gaussian(og.sino_shape, seed=53)).to(DEV).bfloat16()
+    b = torch.from_numpy(inputs.gaussian(og.sino_shape, seed=54)).to(DEV).bfloat16()
+    v = torch.from_numpy(inputs.gaussian(og.vol_shape, seed=55)).to(DEV).bfloat16()
+    ref = v.double().cpu().numpy().ravel() + 0.5 * oracle.adjoint(og, host(a) - host(b)).ravel()
+    ops.adjoint_update(v, a, g, 0.5, sino_b=b)
+    assert rel_l2(host(v).ravel(), ref) <= 4e-3
+
+
+def test_fused_gradient_step_autograd(ops):
+    """operators.gradient_step (fused forward and backward) gives the values and the gradients of the
+    unfused x - alpha A^T (A x - p) composed from the autograd operators."""
+    tr = inputs.jittered_circular_trajectory(24, 2 * math.pi, 75.0, 120.0, 0.5, 0.2, seed=9)
+    shape, sp = (28, 30, 32), (0.5, 0.5, 0.5)
+    g = ops.Geometry.cone_from_positions(shape, sp, (32, 40), (0.6, 0.6), tr.src, tr.det_centre, tr.eu, tr.ev)
+    x0 = torch.from_numpy(inputs.rasterise_ellipsoids(inputs.random_ellipsoids(6, 7.0, 13), shape, sp)).to(DEV)
+    p0 = torch.from_numpy(inputs.uniform(g.sinogram_shape, seed=14)).to(DEV)
+    w = torch.from_numpy(inputs.gaussian(shape, seed=15)).to(DEV)
+    outs, grads = [], []
+    for fused in (True, False):
+        x = x0.clone().requires_grad_(True)
+        p = p0.clone().requires_grad_(True)
+        alpha = torch.tensor(0.01, device=DEV, requires_grad=True)
+        if fused:
+            y = ops.gradient_step(x, p, alpha, g)
+        else:
+            y = x - alpha * ops.project_adjoint(ops.project(x, g) - p, g)
+        (y * w).sum().backward()
+        outs.append(y.detach())
+        grads.append((x.grad, p.grad, alpha.grad))
+    assert rel_l2(host(outs[0]), host(outs[1])) <= 1e-6
+    for a, b in zip(grads[0], grads[1]):
+        assert rel_l2(host(a), host(b)) <= 1e-5
+
+
+def test_unrolled_fused_matches_unfused(ops):
+    from paper_2511_08427_gb300.unrolled import UnrolledGD
+    tr = inputs.jittered_circular_trajectory(30, 2 * math.pi, 75.0, 120.0, 0.5, 0.2, seed=10)
+    shape, sp = (32, 36, 40), (0.5, 0.5, 0.5)
+    g = ops.Geometry.cone_from_positions(shape, sp, (40, 48), (0.6, 0.6), tr.src, tr.det_centre, tr.eu, tr.ev)
+    x_true = torch.from_numpy(inputs.rasterise_ellipsoids(inputs.random_ellipsoids(8, 8.0, 16), shape, sp)).to(DEV)
+    with torch.no_grad():
+        p = ops.forward_project(x_true, g)
+    res = []
+    for fused in (True, False):
+        m = UnrolledGD(g, iterations=5, checkpoint=True, fused=fused)
+        x5 = m(p)
+        ((x5 - x_true) ** 2).sum().backward()
+        res.append((x5.detach(), m.alpha.grad.clone()))
+    assert rel_l2(host(res[0][0]), host(res[1][0])) <= 1e-6
+    assert rel_l2(host(res[0][1]), host(res[1][1])) <= 1e-5
