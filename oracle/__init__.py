@@ -79,6 +79,8 @@ def lib():
         L.or_adjoint.restype = ctypes.c_int
         L.or_bp.argtypes = [og, dp, ctypes.c_int, dp]
         L.or_bp_voxels.argtypes = [og, dp, ctypes.c_int, ctypes.c_long, ip, dp]
+        L.or_fbp_filter.argtypes = [og, ctypes.c_int, dp, dp]
+        L.or_fbp_filter.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -288,6 +290,23 @@ def bp(g: Geometry, sino, weight: int = 0) -> np.ndarray:
     s = g.struct()
     lib().or_bp(ctypes.byref(s), _dp(y), int(weight), _dp(out))
     return out
+
+
+def fbp_filter(g: Geometry, sino, filt: int = 0) -> np.ndarray:
+    """Cosine-weighted (divergent beams), ramp-filtered and scaled sinogram: its BP (weight 1 for
+    perspective geometries, 0 for parallel) is the filtered back-projection. filt 0: Ram-Lak,
+    1: Shepp-Logan."""
+    y = np.ascontiguousarray(np.asarray(sino, dtype=np.float64).reshape(g.sino_shape))
+    out = np.zeros(g.sino_shape)
+    s = g.struct()
+    if lib().or_fbp_filter(ctypes.byref(s), int(filt), _dp(y), _dp(out)) != 0:
+        raise ValueError("singular view")
+    return out
+
+
+def fbp(g: Geometry, sino, filt: int = 0) -> np.ndarray:
+    """Filtered back-projection (FDK for perspective geometries)."""
+    return bp(g, fbp_filter(g, sino, filt), 1 if g.kind == 1 else 0)
 
 
 def bp_voxels(g: Geometry, sino, voxel_ids, weight: int = 0) -> np.ndarray:
