@@ -172,6 +172,19 @@ PYRONN_API int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int 
 PYRONN_API int pyronn_adjoint_update(pyronn_geom_t g, const void *sino, const void *sino_b, double alpha, void *vol,
                                      int dtype, int batch, void *stream);
 
+/* Filtered back-projection filter (Sec. 2.2: x = A^T F^T K F p with a ramp K, as in Listing 1's FDK
+ * pipeline): out = per row, the cosine pre-weight of divergent beams (cos of each pixel's ray to the
+ * detector normal), a direct convolution with the ramp's taps along u (filter 0 Ram-Lak: the ramp
+ * band-limited to the detector's Nyquist frequency; 1 Shepp-Logan: times a sinc window) and the scale
+ * (pi / V) r^2 / tau (r = sid / sdd at the volume centre, tau = detector pitch scaled to the volume
+ * centre; parallel beams: r = 1, tau = du). pyronn_bp of out with weight PYRONN_BP_INV_W2 (divergent)
+ * or PYRONN_BP_PLAIN (parallel) is the reconstruction of a [0, 2 pi) divergent or [0, pi) parallel
+ * scan with V uniformly spaced views. sino and out are [batch][V][Nv][Nu] of one element type and may
+ * be the same buffer; Nu <= 4096. Asynchronous on stream; status code as elsewhere. */
+typedef enum { PYRONN_FILTER_RAM_LAK = 0, PYRONN_FILTER_SHEPP_LOGAN = 1 } pyronn_fbp_filter_kind;
+PYRONN_API int pyronn_fbp_filter(pyronn_geom_t g, const void *sino, void *out, int filter, int dtype, int batch,
+                                 void *stream);
+
 /* Voxel-driven back-projection (Sec. 2.1): vol = BP sino, overwriting vol; weight is a
  * pyronn_bp_weight. Not the transpose of pyronn_fp. */
 PYRONN_API int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, int weight, void *stream);

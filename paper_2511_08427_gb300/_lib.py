@@ -58,6 +58,7 @@ SIGNATURES = [
     ("pyronn_fp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_adjoint", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_adjoint_update", _c_int, [_vp, _vp, _vp, ctypes.c_double, _vp, _c_int, _c_int, _vp]),
+    ("pyronn_fbp_filter", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_bp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_bp_transpose", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_adjoint_noalloc", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),

@@ -180,6 +180,49 @@ int finish(pyronn_geom *g, pyronn_geom_t *out) {
 }  // namespace
 
 // Build the FP32 device records from the FP64 views.
+// Per-view FBP constants (see or_fbp_filter for the definitions): perspective views give the source
+// -> pixel basis inv(M') (columns du eu, dv ev, D0 - S), sdd = 1 / |P_3| (P's third row spans w = 0 at
+// the source to w = 1 on the detector), r = w(volume centre) and tau = r |du eu|.
+int ensure_fbp(pyronn_geom *g) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->d_fbp) return PYRONN_OK;
+    const int V = g->n_views;
+    const double pi = 3.14159265358979323846;
+    std::vector<FbpRec> rec(V);
+    for (int n = 0; n < V; ++n) {
+        FbpRec &f = rec[n];
+        double scale;
+        if (g->kind == 1) {
+            const double *r = &g->views[12 * (size_t)n];
+            const double *x = &g->views_ext[(size_t)n * VIEW64_STRIDE];
+            const double nn = std::sqrt(r[8] * r[8] + r[9] * r[9] + r[10] * r[10]);
+            const double ratio = x[11];   // w at the volume centre
+            const double pu = std::sqrt(x[15] * x[15] + x[16] * x[16] + x[17] * x[17]);
+            const double tau = ratio * pu;
+            scale = pi / V * ratio * ratio / tau;
+            f.sdd = (float)(1.0 / nn);
+            for (int i = 0; i < 3; ++i) {
+                f.bu[i] = (float)x[15 + i];
+                f.bv[i] = (float)x[18 + i];
+                f.b0[i] = (float)x[21 + i];
+            }
+        } else {
+            scale = pi / V / g->du;
+            f.sdd = 0.0f;
+            for (int i = 0; i < 3; ++i) f.b0[i] = f.bu[i] = f.bv[i] = 0.0f;
+        }
+        f.scale = (float)scale;
+    }
+    cudaError_t e = cudaMalloc(&g->d_fbp, sizeof(FbpRec) * (size_t)V);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_fbp, rec.data(), sizeof(FbpRec) * (size_t)V, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(g->d_fbp);
+        g->d_fbp = nullptr;
+        return set_error(PYRONN_CUDA_ERROR, "FBP constants: %s", cudaGetErrorString(e));
+    }
+    return PYRONN_OK;
+}
+
 int finalize_geometry(pyronn_geom *g) {
     const int V = g->n_views;
     g->fp_rec.assign(V, FpRec{});
@@ -504,7 +547,7 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
     clear_error();
     if (!g) return PYRONN_OK;
     // device buffers are freed on the device they were allocated on
-    if (g->d_fp || g->d_scratch || g->d_stage_in || g->d_stage_out || g->d_upd_sino || g->d_upd_vol) {
+    if (g->d_fp || g->d_scratch || g->d_stage_in || g->d_stage_out || g->d_upd_sino || g->d_upd_vol || g->d_fbp) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (g->device >= 0 && g->device != cur) cudaSetDevice(g->device);
@@ -516,6 +559,7 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
         cudaFree(g->d_stage_in);
         cudaFree(g->d_stage_out);
         cudaFree(g->d_upd_sino);
+        cudaFree(g->d_fbp);
         cudaFree(g->d_upd_vol);
         if (g->device >= 0 && cur >= 0 && g->device != cur) cudaSetDevice(cur);
     }

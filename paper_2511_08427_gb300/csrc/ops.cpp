@@ -276,6 +276,19 @@ int pyronn_adjoint_update(pyronn_geom_t g, const void *sino, const void *sino_b,
     return cuda_rc(launch_axpy(vol, g->d_upd_vol, (float)alpha, nv, dtype, stream), "update launch");
 }
 
+int pyronn_fbp_filter(pyronn_geom_t g, const void *sino, void *out, int filter, int dtype, int batch, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(sino, "sino")) || (rc = check_ptr(out, "out"))) return rc;
+    if (filter != PYRONN_FILTER_RAM_LAK && filter != PYRONN_FILTER_SHEPP_LOGAN)
+        return set_error(PYRONN_INVALID_ARG, "unknown filter %d", filter);
+    if (g->nu > 4096) return set_error(PYRONN_INVALID_ARG, "FBP rows longer than 4096 pixels are not supported");
+    if ((rc = ensure_fbp(g))) return rc;
+    OpParams p = make_params(g, batch);
+    return cuda_rc(launch_fbp_filter(p, g->d_fbp, filter, sino, out, dtype, stream), "FBP filter launch");
+}
+
 int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, int weight, void *stream) {
     clear_error();
     int rc = common_checks(g, dtype, batch);

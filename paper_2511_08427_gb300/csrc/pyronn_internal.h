@@ -24,6 +24,13 @@ struct FpRec {
     float B0[3], Bu[3], Bv[3];
 };
 
+// Filtered back-projection filter constants of one view (host FP64, stored FP32).
+struct FbpRec {
+    float scale;               // (pi / V) r^2 / tau: r = sid / sdd, tau = detector pitch at the volume centre
+    float sdd;                 // source-detector distance, mm (0: parallel beam, no cosine weight)
+    float b0[3], bu[3], bv[3]; // source -> pixel (u, v) = b0 + u bu + v bv, mm
+};
+
 // Projection of centred voxel indices (i - (Nx-1)/2, j - (Ny-1)/2, k - (Nz-1)/2, 1) to centred
 // detector coordinates times depth: (u_c w, v_c w, w); u = u_c + (Nu-1)/2. Row-major 3 x 4.
 struct BpRec {
@@ -164,6 +171,7 @@ struct pyronn_geom {
     double *d_views64 = nullptr;
     void *d_scratch = nullptr;     // FP32 accumulation buffer for reduced-precision adjoints
     size_t scratch_bytes = 0;
+    pyronn::FbpRec *d_fbp = nullptr;   // FBP filter constants per view (uploaded on first use)
     void *d_upd_sino = nullptr;    // work buffers of pyronn_adjoint_update on the unfused kernels
     void *d_upd_vol = nullptr;
     size_t upd_sino_bytes = 0, upd_vol_bytes = 0;
@@ -200,6 +208,9 @@ int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void 
 int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int launch_adjoint_brick_batched(const PlanLaunch &L, int dtype, int grid, void *stream);
 int launch_residual(const void *a, const void *b, void *out, long long n, int dtype, void *stream);
+int launch_fbp_filter(const OpParams &p, const FbpRec *rec, int filter, const void *in, void *out, int dtype,
+                      void *stream);
+int ensure_fbp(pyronn_geom *g);   // builds and uploads d_fbp (host FP64)
 int launch_axpy(void *vol, const void *w, float alpha, long long n, int dtype, void *stream);
 int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int adjoint_slab_batched_occupancy(size_t smem, int *blocks_per_sm);

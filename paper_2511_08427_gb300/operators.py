@@ -277,6 +277,31 @@ def adjoint_update(vol: torch.Tensor, sino: torch.Tensor, g: Geometry, alpha: fl
     return vol
 
 
+FILTER_RAM_LAK, FILTER_SHEPP_LOGAN = 0, 1
+
+
+def fbp_filter(sino: torch.Tensor, g: Geometry, filter: int = FILTER_RAM_LAK,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """Cosine-weighted (divergent beams), ramp-filtered and scaled sinogram (pyronn_fbp_filter): its
+    back-projection with weight BP_INV_W2 (divergent) or BP_PLAIN (parallel) is the filtered
+    back-projection (Sec. 2.2). out may be sino itself."""
+    dt = _check(sino, "sinogram")
+    sino = sino.contiguous()
+    lead, nb = _batch(sino, _sino_dims(g), "sinogram")
+    if out is None:
+        out = torch.empty_like(sino)
+    with torch.cuda.device(sino.device):
+        check(lib().pyronn_fbp_filter(g.handle, sino.data_ptr(), out.data_ptr(), int(filter), dt, nb,
+                                      _stream_ptr(sino.device)))
+    return out
+
+
+def fbp(sino: torch.Tensor, g: Geometry, filter: int = FILTER_RAM_LAK) -> torch.Tensor:
+    """Filtered back-projection (FDK for divergent beams) of a full scan: fbp_filter, then the voxel-driven
+    back-projection with the matching weight."""
+    return back_project(fbp_filter(sino, g, filter), g, BP_INV_W2 if g.kind == 1 else BP_PLAIN)
+
+
 def back_project(sino: torch.Tensor, g: Geometry, weight: int = BP_PLAIN, out: torch.Tensor | None = None):
     """vol = BP sino (voxel-driven back-projection, Sec. 2.1); weight BP_PLAIN or BP_INV_W2."""
     dt = _check(sino, "sinogram")
