@@ -1,6 +1,6 @@
 """Run one operator on a cone-beam workload a few times (for profilers such as Nsight Compute).
 
-    python -m paper_2511_08427_gb300.profile_ops {fp,adj,bp} [N] [--repeat R] [--dtype float32|bfloat16]
+    python -m paper_2511_08427_gb300.profile_ops {fp,adj,bp,fbp} [N] [--repeat R] [--dtype float32|bfloat16]
                                                  [--accum 0|1|2] [--time]
 
 N = 256: 256^3 volume (0.5 mm voxels), 360 views over 2 pi, 512 x 512 detector (0.6 mm),
@@ -33,7 +33,7 @@ def workload(n: int):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["fp", "adj", "bp"])
+    ap.add_argument("op", choices=["fp", "adj", "bp", "fbp"])
     ap.add_argument("n", nargs="?", type=int, default=256)
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--dtype", default="float32", choices=["float32", "bfloat16", "float16"])
@@ -45,6 +45,7 @@ def main():
     g.set_tuning(ops.TUNE_ADJ_ACCUM, a.accum)
     vol = torch.from_numpy(vol_np).cuda().to(dt)
     sino = torch.empty(sshape, device="cuda", dtype=dt)
+    sino2 = torch.empty_like(sino) if a.op == "fbp" else None
     if a.op != "fp":
         sino.copy_(torch.randn(sshape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(22)))
 
@@ -53,6 +54,8 @@ def main():
             ops.forward_project(vol, g, out=sino)
         elif a.op == "adj":
             ops.adjoint(sino, g, out=vol)
+        elif a.op == "fbp":
+            ops.fbp_filter(sino, g, out=sino2)
         else:
             ops.back_project(sino, g, out=vol)
 
