@@ -249,7 +249,10 @@ PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void 
  * automatic (= 3 where usable, else 2), 1 one-thread-per-ray read-only-cache kernel, 2 slab-staged
  * shared-memory kernel filled by thread loads (falls back to 1 when the staged box cannot fit),
  * 3 slab-staged kernel filled by TMA tensor copies (needs a row pitch that is a multiple of 16
- * bytes; falls back to 2). op 1 = matched adjoint:
+ * bytes; falls back to 2), 4 one thread per ray with texture gathers from a tiled 2D copy of the
+ * volume (3D FP32 within the device's gather-texture limits, else as 0; the copy belongs to the
+ * geometry, so forward projections with one geometry on different streams must not overlap).
+ * op 1 = matched adjoint:
  * variant 0 automatic (= 3 where its box fits, else 2), 1 one-thread-per-ray FP32 global atomics,
  * 2 output-stationary bricks accumulated in shared memory, 3 slab-ordered: detector tiles march
  * the volume like the forward projector, scatter into shared-memory slab boxes and add each box to
@@ -293,7 +296,8 @@ PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
 PYRONN_API int pyronn_geom_read_flags(pyronn_geom_t g, int *out, int reset);
 
 /* Forward-projector configuration that would be used for element type dtype (host computation,
- * no GPU needed), 16 ints: [0] kernel (1 direct, 2 slab thread-staged, 3 slab TMA-staged),
+ * no GPU needed), 16 ints: [0] kernel (1 direct, 2 slab thread-staged, 3 slab TMA-staged, 4 texture
+ * gather),
  * [1] slab depth, [2] guard planes, [3] first slab plane, [4..12] TMA box (x, y, z) for march
  * axes x, y, z, [13] elements per TMA buffer, [14] dynamic shared memory bytes per CTA,
  * [15] thread-staged box capacity (elements). */

@@ -126,7 +126,11 @@ int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch
     OpParams p = make_params(g, batch);
     if (g->fp_variant == 1)
         return cuda_rc(launch_fp_direct(p, vol, sino, dtype, stream), "forward projection launch");
-    if (g->fp_variant == 0 || g->fp_variant == 3) {
+    if (g->fp_variant == 4 && fp_tex_usable(g, batch, dtype)) {
+        std::lock_guard<std::mutex> lk(g->mu);
+        return cuda_rc(launch_fp_tex(g, p, vol, sino, stream), "forward projection launch");
+    }
+    if (g->fp_variant == 0 || g->fp_variant == 3 || g->fp_variant == 4) {
         const FpTmaBox &tb = tma_cfg(g, dtype);
         if (tb.depth > 0) return cuda_rc(launch_fp_tma(p, tb, vol, sino, dtype, stream), "forward projection launch");
     }
@@ -142,7 +146,8 @@ int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out) {
     const FpSlabCfg &sc = fp_cfg(g);
     int kernel = 1;
     if (g->fp_variant == 1) kernel = 1;
-    else if ((g->fp_variant == 0 || g->fp_variant == 3) && tb.depth > 0) kernel = 3;
+    else if (g->fp_variant == 4 && fp_tex_usable(g, 1, dtype)) kernel = 4;
+    else if ((g->fp_variant == 0 || g->fp_variant == 3 || g->fp_variant == 4) && tb.depth > 0) kernel = 3;
     else if (sc.valid) kernel = 2;
     out[0] = kernel;
     out[1] = kernel == 3 ? tb.depth : sc.depth;
@@ -207,7 +212,8 @@ int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
     if (op < 0 || op > 2) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
-    if (variant < 0 || variant > (op == 2 ? 2 : 3)) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
+    const int vmax = op == 0 ? 4 : (op == 1 ? 3 : 2);
+    if (variant < 0 || variant > vmax) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
     if (op == 0) g->fp_variant = variant;
     else if (op == 1) g->adj_variant = variant;
     else g->bp_variant = variant;

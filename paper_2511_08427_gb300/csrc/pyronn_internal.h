@@ -172,6 +172,10 @@ struct pyronn_geom {
     void *d_scratch = nullptr;     // FP32 accumulation buffer for reduced-precision adjoints
     size_t scratch_bytes = 0;
     pyronn::FbpRec *d_fbp = nullptr;   // FBP filter constants per view (uploaded on first use)
+    void *tex_arr = nullptr;       // tiled gather texture of the texture projector (cudaArray_t)
+    unsigned long long tex_obj = 0;    // its texture object
+    void *d_tex_org = nullptr;     // tile origins (float2 per tile)
+    int tex_batch = 0;             // volumes the array holds
     void *d_upd_sino = nullptr;    // work buffers of pyronn_adjoint_update on the unfused kernels
     void *d_upd_vol = nullptr;
     size_t upd_sino_bytes = 0, upd_vol_bytes = 0;
@@ -185,7 +189,7 @@ struct pyronn_geom {
     pyronn::FpTmaBox tma_cfg[3] = {};   // per dtype
     pyronn::Tuning tuning;
     int tma_ready[3] = {0, 0, 0};
-    int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged (thread loads), 3 slab-staged (TMA)
+    int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged (thread loads), 3 slab-staged (TMA), 4 texture gather
     int adj_variant = 0;           // 0 auto, 1 atomic scatter, 2 output-stationary bricks, 3 slab-ordered
     pyronn::AdjSlabCfg adj_cfg{};
     int adj_cfg_ready = 0;
@@ -211,6 +215,8 @@ int launch_residual(const void *a, const void *b, void *out, long long n, int dt
 int launch_fbp_filter(const OpParams &p, const FbpRec *rec, int filter, const void *in, void *out, int dtype,
                       void *stream);
 int ensure_fbp(pyronn_geom *g);   // builds and uploads d_fbp (host FP64)
+bool fp_tex_usable(const pyronn_geom *g, int batch, int dtype);
+int launch_fp_tex(pyronn_geom *g, const OpParams &p, const void *vol, void *sino, void *stream);
 int launch_axpy(void *vol, const void *w, float alpha, long long n, int dtype, void *stream);
 int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int adjoint_slab_batched_occupancy(size_t smem, int *blocks_per_sm);

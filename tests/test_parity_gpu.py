@@ -62,7 +62,7 @@ def oracle_fp(case, x):
 # small cases: every geometry, every kernel variant, every storage type
 # ------------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
 def test_fp_matches_oracle(ops, case, variant):
     g = case.library_geometry()
@@ -286,6 +286,22 @@ def test_custom_step(ops, dt):
         assert rel_l2(host(ops.forward_project(to_dev(x), g)), oracle.fp(og, x)) <= 1e-5
     y = inputs.gaussian(og.sino_shape, seed=2)
     assert rel_l2(host(ops.adjoint(to_dev(y), g)), oracle.adjoint(og, y)) <= 1e-5
+
+
+def test_texture_gather_projector_batch(ops):
+    """Texture-gather forward projector (variant 4): a batch of two volumes (each plane a tile of one
+    gather texture, with zero tiles between the volumes) equals the per-volume projections and the
+    oracle."""
+    case = SMALL[2]
+    g = case.library_geometry()
+    g.set_variant(0, 4)
+    assert g.fp_config()["kernel"] == 4
+    x1, x2 = case.phantom(seed=7), case.phantom(seed=8)
+    pb = host(ops.forward_project(to_dev(np.stack([x1, x2])), g))
+    for i, x in enumerate((x1, x2)):
+        assert rel_l2(pb[i], oracle_fp(case, x)) <= 1e-5
+        assert rel_l2(pb[i], host(ops.forward_project(to_dev(x), g))) <= 1e-7
+    assert g.read_flags()[:4] == [0, 0, 0, 0]
 
 
 def test_many_views_times_batch_splits_launches(ops):
