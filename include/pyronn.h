@@ -185,6 +185,36 @@ typedef enum { PYRONN_FILTER_RAM_LAK = 0, PYRONN_FILTER_SHEPP_LOGAN = 1 } pyronn
 PYRONN_API int pyronn_fbp_filter(pyronn_geom_t g, const void *sino, void *out, int filter, int dtype, int batch,
                                  void *stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Acquisition-artifact simulation (Sec. 2.4). Sinograms [batch][V][Nv][Nu] of element type dtype
+ * on the device; every random quantity is passed in (device arrays), so the calls are
+ * deterministic. Asynchronous on stream; status code as elsewhere.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Detector jitter: every detector row (axis 0: out[v][u] = sino[v][u - s], one int32 shift per
+ * (item, view, row): [batch][V][Nv]) or column (axis 1: out[v][u] = sino[v - s][u], shifts
+ * [batch][V][Nu]) moved by its shift in pixels, zero where the source lies outside. Not in place. */
+PYRONN_API int pyronn_sim_detector_jitter(pyronn_geom_t g, const void *sino, void *out, const int32_t *shifts,
+                                          int axis, int dtype, int batch, void *stream);
+
+/* Gaussian noise: out = sino + mean + std * noise, noise an FP32 array of standard-normal samples
+ * shaped like the sinogram. out may be sino. */
+PYRONN_API int pyronn_sim_gaussian_noise(pyronn_geom_t g, const void *sino, void *out, const float *noise, double mean,
+                                         double std, int dtype, int batch, void *stream);
+
+/* Ring artifacts: out = sino, except detector columns columns[c] (int32, c < n_columns) of views
+ * view_begin .. view_end - 1, which are multiplied by gains[c] (FP32; 0 = dead element). Columns
+ * outside [0, Nu) are ignored. out may be sino. */
+PYRONN_API int pyronn_sim_ring(pyronn_geom_t g, const void *sino, void *out, const int32_t *columns, const float *gains,
+                               int n_columns, int view_begin, int view_end, int dtype, int batch, void *stream);
+
+/* Gantry motion blur: each projection convolved with a line kernel of `length` samples (1 .. 1024),
+ * unit total weight, rotated to its view's angle angles[view] (FP32 radians, [V]):
+ * out(u, v) = (1 / L) sum_j bilinear(sino, u + t_j cos a, v + t_j sin a), t_j = j - (L - 1) / 2, zero
+ * outside the detector. Not in place. */
+PYRONN_API int pyronn_sim_motion_blur(pyronn_geom_t g, const void *sino, void *out, const float *angles, int length,
+                                      int dtype, int batch, void *stream);
+
 /* Voxel-driven back-projection (Sec. 2.1): vol = BP sino, overwriting vol; weight is a
  * pyronn_bp_weight. Not the transpose of pyronn_fp. */
 PYRONN_API int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, int weight, void *stream);

@@ -59,6 +59,10 @@ SIGNATURES = [
     ("pyronn_adjoint", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_adjoint_update", _c_int, [_vp, _vp, _vp, ctypes.c_double, _vp, _c_int, _c_int, _vp]),
     ("pyronn_fbp_filter", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
+    ("pyronn_sim_detector_jitter", _c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
+    ("pyronn_sim_gaussian_noise", _c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _c_int, _c_int, _vp]),
+    ("pyronn_sim_ring", _c_int, [_vp, _vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _vp]),
+    ("pyronn_sim_motion_blur", _c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_bp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_bp_transpose", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("pyronn_adjoint_noalloc", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),

@@ -295,6 +295,69 @@ int pyronn_fbp_filter(pyronn_geom_t g, const void *sino, void *out, int filter, 
     return cuda_rc(launch_fbp_filter(p, g->d_fbp, filter, sino, out, dtype, stream), "FBP filter launch");
 }
 
+// ---------------------------------------------------------------------------------------------
+// acquisition artifacts (Sec. 2.4)
+// ---------------------------------------------------------------------------------------------
+
+int pyronn_sim_detector_jitter(pyronn_geom_t g, const void *sino, void *out, const int32_t *shifts, int axis, int dtype,
+                               int batch, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(sino, "sino")) || (rc = check_ptr(out, "out"))) return rc;
+    if (!shifts) return set_error(PYRONN_INVALID_ARG, "null shifts");
+    if (axis != 0 && axis != 1) return set_error(PYRONN_INVALID_ARG, "axis must be 0 (rows) or 1 (columns)");
+    if (sino == out) return set_error(PYRONN_INVALID_ARG, "jitter cannot run in place");
+    const long long n = (long long)batch * g->n_views * g->nv * g->nu;
+    return cuda_rc(launch_sim_jitter(sino, out, shifts, axis, g->nu, g->nv, n, dtype, stream), "jitter launch");
+}
+
+int pyronn_sim_gaussian_noise(pyronn_geom_t g, const void *sino, void *out, const float *noise, double mean, double sd,
+                              int dtype, int batch, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(sino, "sino")) || (rc = check_ptr(out, "out"))) return rc;
+    if (!noise) return set_error(PYRONN_INVALID_ARG, "null noise");
+    if (!std::isfinite(mean) || !std::isfinite(sd)) return set_error(PYRONN_INVALID_ARG, "mean and std must be finite");
+    const long long n = (long long)batch * g->n_views * g->nv * g->nu;
+    return cuda_rc(launch_sim_noise(sino, out, noise, (float)mean, (float)sd, n, dtype, stream), "noise launch");
+}
+
+int pyronn_sim_ring(pyronn_geom_t g, const void *sino, void *out, const int32_t *columns, const float *gains,
+                    int n_columns, int view_begin, int view_end, int dtype, int batch, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(sino, "sino")) || (rc = check_ptr(out, "out"))) return rc;
+    if (n_columns < 0 || (n_columns > 0 && (!columns || !gains)))
+        return set_error(PYRONN_INVALID_ARG, "columns / gains missing");
+    if (view_begin < 0 || view_end > g->n_views || view_begin > view_end)
+        return set_error(PYRONN_INVALID_ARG, "view range [%d, %d) outside [0, %d]", view_begin, view_end, g->n_views);
+    const size_t bytes = dtype_size(dtype) * (size_t)batch * g->n_views * g->nv * g->nu;
+    if (out != sino) {
+        cudaError_t e = cudaMemcpyAsync(out, sino, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_rc((int)e, "ring copy");
+    }
+    if (n_columns == 0 || view_end == view_begin) return PYRONN_OK;
+    return cuda_rc(launch_sim_ring(out, out, columns, gains, n_columns, g->nu, g->nv, g->n_views, view_begin, view_end,
+                                   batch, dtype, stream),
+                   "ring launch");
+}
+
+int pyronn_sim_motion_blur(pyronn_geom_t g, const void *sino, void *out, const float *angles, int length, int dtype,
+                           int batch, void *stream) {
+    clear_error();
+    int rc = common_checks(g, dtype, batch);
+    if (rc) return rc;
+    if ((rc = check_ptr(sino, "sino")) || (rc = check_ptr(out, "out"))) return rc;
+    if (!angles) return set_error(PYRONN_INVALID_ARG, "null angles");
+    if (length < 1 || length > 1024) return set_error(PYRONN_INVALID_ARG, "kernel length %d out of [1, 1024]", length);
+    if (sino == out) return set_error(PYRONN_INVALID_ARG, "motion blur cannot run in place");
+    const long long n = (long long)batch * g->n_views * g->nv * g->nu;
+    return cuda_rc(launch_sim_blur(sino, out, angles, length, g->nu, g->nv, g->n_views, n, dtype, stream), "blur launch");
+}
+
 int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch, int weight, void *stream) {
     clear_error();
     int rc = common_checks(g, dtype, batch);

@@ -216,6 +216,14 @@ int launch_fbp_filter(const OpParams &p, const FbpRec *rec, int filter, const vo
                       void *stream);
 int ensure_fbp(pyronn_geom *g);   // builds and uploads d_fbp (host FP64)
 bool fp_tex_usable(const pyronn_geom *g, int batch, int dtype);
+int launch_sim_jitter(const void *in, void *out, const int *shifts, int axis, int nu, int nv, long long n, int dtype,
+                      void *stream);
+int launch_sim_noise(const void *in, void *out, const float *noise, float mean, float sd, long long n, int dtype,
+                     void *stream);
+int launch_sim_ring(const void *in, void *out, const int *cols, const float *gains, int ncol, int nu, int nv, int n_views,
+                    int v0, int v1, int batch, int dtype, void *stream);
+int launch_sim_blur(const void *in, void *out, const float *angles, int length, int nu, int nv, int n_views, long long n,
+                    int dtype, void *stream);
 int launch_fp_tex(pyronn_geom *g, const OpParams &p, const void *vol, void *sino, void *stream);
 int launch_axpy(void *vol, const void *w, float alpha, long long n, int dtype, void *stream);
 int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);

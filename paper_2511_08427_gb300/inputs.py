@@ -175,6 +175,18 @@ def poisson_log_sinogram_torch(p, i0: float, seed: int, scale_to_max: float | No
     return -torch.log(torch.clamp(c, min=1.0) / i0)
 
 
+def jitter_shifts(shape, max_shift: int, seed: int) -> np.ndarray:
+    """Integer detector shifts uniform in [-max_shift, max_shift] (int32), e.g. shape (V, Nv) per row."""
+    return np.random.default_rng(seed).integers(-max_shift, max_shift + 1, size=shape).astype(np.int32)
+
+
+def ring_columns(nu: int, count: int, seed: int, gain_lo: float = 0.0, gain_hi: float = 1.2):
+    """`count` distinct detector columns and their gains uniform in [gain_lo, gain_hi]."""
+    rng = np.random.default_rng(seed)
+    cols = rng.choice(nu, size=count, replace=False).astype(np.int32)
+    return cols, (gain_lo + (gain_hi - gain_lo) * rng.random(count)).astype(np.float32)
+
+
 @dataclass
 class Trajectory:
     """Per-view source position, detector centre and detector axes, world mm (float64, V x 3 each)."""

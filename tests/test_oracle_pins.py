@@ -545,3 +545,36 @@ def test_fdk_cosine_weight_from_independent_geometry(oracle_lib):
         conv = np.array([h[nd + (k - np.arange(nd))].sum() for k in range(nd)])
         expected = math.pi * r * r / (du * r) * conv
         assert np.abs(q - expected).max() < 1e-10 * np.abs(expected).max(), v
+
+
+# ------------------------------------------------------------------------------------------------
+# acquisition-artifact simulations (Sec. 2.4)
+# ------------------------------------------------------------------------------------------------
+
+def test_artifact_references():
+    """Jitter by zero is the identity and by s moves every value s pixels (zero fill); ring gains touch
+    only the chosen columns and views; the blur kernel has unit weight (interior sums preserved),
+    blurs a point into a segment of L pixels of weight 1/L along the view angle (u at 0, v at pi/2),
+    and L = 1 is the identity."""
+    from oracle import artifacts as A
+    rng = np.random.default_rng(0)
+    p = rng.random((3, 9, 11))
+    assert np.array_equal(A.detector_jitter(p, np.zeros((3, 9), int), 0), p)
+    s = np.full((3, 9), 2)
+    j = A.detector_jitter(p, s, 0)
+    assert np.array_equal(j[:, :, 2:], p[:, :, :-2]) and not j[:, :, :2].any()
+    j = A.detector_jitter(p, np.full((3, 11), -1), 1)
+    assert np.array_equal(j[:, :-1, :], p[:, 1:, :]) and not j[:, -1, :].any()
+    r = A.ring_artifacts(p, [3, 7], [0.0, 1.5], 1, 3)
+    assert np.array_equal(r[0], p[0]) and not r[1:, :, 3].any()
+    assert np.allclose(r[1:, :, 7], 1.5 * p[1:, :, 7]) and np.array_equal(r[:, :, 5], p[:, :, 5])
+    assert np.allclose(A.motion_blur(p, [0.3, 1.0, 2.0], 1), p)
+    d = np.zeros((2, 15, 15))
+    d[:, 7, 7] = 1.0
+    b = A.motion_blur(d, [0.0, math.pi / 2], 5)
+    row = np.zeros(15)
+    row[5:10] = 0.2
+    assert np.allclose(b[0, 7], row) and np.allclose(b[0].sum(), 1.0)
+    assert np.allclose(b[1][:, 7], row) and np.allclose(b[1].sum(), 1.0)
+    b = A.motion_blur(d, [0.7, 2.1], 4)
+    assert np.allclose(b.sum(axis=(1, 2)), 1.0)
