@@ -120,6 +120,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(values, world: int, device=None):
+    """Element-wise maximum of per-rank timings over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_rate(units_per_rank: float, world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput in G units/s: every rank processed units_per_rank per step."""
+    return world * units_per_rank * steps / seconds / 1e9
+
+
 def build_inputs(seed_vol=3):
     from paper_2511_08427_gb300 import inputs
     vol = inputs.rasterise_ellipsoids(inputs.random_ellipsoids(20, 64.0, seed_vol), (256, 256, 256),
@@ -330,13 +345,10 @@ def run_gpu(args):
     fp_ms = np.array([e[0].elapsed_time(e[1]) for e in evs])
     adj_ms = np.array([e[1].elapsed_time(e[2]) for e in evs])
     bp_ms = np.array([e[2].elapsed_time(e[3]) for e in evs])
-    stats = torch.tensor([total_ms, fp_ms.sum(), adj_ms.sum(), bp_ms.sum()], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(stats, op=dist.ReduceOp.MAX)
-    total_ms, fp_sum, adj_sum, bp_sum = [float(x) for x in stats.cpu()]
+    total_ms, fp_sum, adj_sum, bp_sum = max_over_ranks([total_ms, fp_ms.sum(), adj_ms.sum(), bp_ms.sum()], world, dev)
     K = args.steps
-    fp_rate = world * n_samples * K / (fp_sum * 1e-3) / 1e9
-    bp_rate = world * n_updates * K / (bp_sum * 1e-3) / 1e9
+    fp_rate = job_rate(n_samples, world, K, fp_sum * 1e-3)
+    bp_rate = job_rate(n_updates, world, K, bp_sum * 1e-3)
 
     # one gradient-descent iteration x <- x - alpha A^T (A x - p) on this workload, from x = 0.9 x_true:
     # unfused (projection, residual, adjoint, axpy) and fused (projection + pyronn_adjoint_update)
@@ -384,7 +396,8 @@ def run_gpu(args):
     for _ in range(n_e2e):
         e2e_call()
     e2e_s = (time.perf_counter() - t0) / n_e2e
-    e2e_rate = world * n_samples / e2e_s / 1e9
+    e2e_s = max_over_ranks([e2e_s], world, dev)[0]
+    e2e_rate = job_rate(n_samples, world, 1, e2e_s)
 
     peaks, peak_src = measured_peaks()
     clk = clocks.summary()
