@@ -308,7 +308,6 @@ int finalize_geometry(pyronn_geom *g) {
     g->fp_cfg_ready = 0;
     g->tma_ready[0] = g->tma_ready[1] = g->tma_ready[2] = 0;
     g->adj_cfg_ready = 0;
-    g->adj_cfg_ready = 0;
     return PYRONN_OK;
 }
 
