@@ -39,7 +39,7 @@ int common_checks(pyronn_geom_t g, int dtype, int batch) {
     if (nvox >= (1LL << 31) || (long long)g->nu * g->nv >= (1LL << 31))
         return set_error(PYRONN_INVALID_ARG, "volume or detector too large for 32-bit in-volume indexing");
     if (nsino * batch <= 0 || nvox * batch <= 0) return set_error(PYRONN_INVALID_ARG, "empty operand");
-    return ensure_device(g);
+    return PYRONN_OK;   // the device tables are set up by the caller once every argument has been checked
 }
 
 int cuda_rc(int e, const char *what) {
@@ -123,6 +123,7 @@ int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch
     int rc = common_checks(g, dtype, batch);
     if (rc) return rc;
     if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
+    if ((rc = ensure_device(g))) return rc;
     OpParams p = make_params(g, batch);
     if (g->fp_variant == 1)
         return cuda_rc(launch_fp_direct(p, vol, sino, dtype, stream), "forward projection launch");
@@ -225,6 +226,7 @@ int pyronn_adjoint(pyronn_geom_t g, const void *sino, void *vol, int dtype, int 
     int rc = common_checks(g, dtype, batch);
     if (rc) return rc;
     if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
+    if ((rc = ensure_device(g))) return rc;
     OpParams p = make_params(g, batch);
     if (g->adj_variant == 0 || g->adj_variant == 3) {
         const AdjSlabCfg &ac = adj_cfg(g);
@@ -255,6 +257,7 @@ int pyronn_adjoint_update(pyronn_geom_t g, const void *sino, const void *sino_b,
     if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
     if (sino_b && (rc = check_ptr(sino_b, "sino_b"))) return rc;
     if (!std::isfinite(alpha)) return set_error(PYRONN_INVALID_ARG, "alpha must be finite");
+    if ((rc = ensure_device(g))) return rc;
     OpParams p = make_params(g, batch);
     if (g->adj_variant == 0 || g->adj_variant == 3) {
         const AdjSlabCfg &ac = adj_cfg(g);
@@ -290,7 +293,7 @@ int pyronn_fbp_filter(pyronn_geom_t g, const void *sino, void *out, int filter, 
     if (filter != PYRONN_FILTER_RAM_LAK && filter != PYRONN_FILTER_SHEPP_LOGAN)
         return set_error(PYRONN_INVALID_ARG, "unknown filter %d", filter);
     if (g->nu > 4096) return set_error(PYRONN_INVALID_ARG, "FBP rows longer than 4096 pixels are not supported");
-    if ((rc = ensure_fbp(g))) return rc;
+    if ((rc = ensure_device(g)) || (rc = ensure_fbp(g))) return rc;
     OpParams p = make_params(g, batch);
     return cuda_rc(launch_fbp_filter(p, g->d_fbp, filter, sino, out, dtype, stream), "FBP filter launch");
 }
@@ -309,6 +312,7 @@ int pyronn_sim_detector_jitter(pyronn_geom_t g, const void *sino, void *out, con
     if (axis != 0 && axis != 1) return set_error(PYRONN_INVALID_ARG, "axis must be 0 (rows) or 1 (columns)");
     if (sino == out) return set_error(PYRONN_INVALID_ARG, "jitter cannot run in place");
     const long long n = (long long)batch * g->n_views * g->nv * g->nu;
+    if ((rc = ensure_device(g))) return rc;
     return cuda_rc(launch_sim_jitter(sino, out, shifts, axis, g->nu, g->nv, n, dtype, stream), "jitter launch");
 }
 
@@ -321,6 +325,7 @@ int pyronn_sim_gaussian_noise(pyronn_geom_t g, const void *sino, void *out, cons
     if (!noise) return set_error(PYRONN_INVALID_ARG, "null noise");
     if (!std::isfinite(mean) || !std::isfinite(sd)) return set_error(PYRONN_INVALID_ARG, "mean and std must be finite");
     const long long n = (long long)batch * g->n_views * g->nv * g->nu;
+    if ((rc = ensure_device(g))) return rc;
     return cuda_rc(launch_sim_noise(sino, out, noise, (float)mean, (float)sd, n, dtype, stream), "noise launch");
 }
 
@@ -334,6 +339,7 @@ int pyronn_sim_ring(pyronn_geom_t g, const void *sino, void *out, const int32_t 
         return set_error(PYRONN_INVALID_ARG, "columns / gains missing");
     if (view_begin < 0 || view_end > g->n_views || view_begin > view_end)
         return set_error(PYRONN_INVALID_ARG, "view range [%d, %d) outside [0, %d]", view_begin, view_end, g->n_views);
+    if ((rc = ensure_device(g))) return rc;
     const size_t bytes = dtype_size(dtype) * (size_t)batch * g->n_views * g->nv * g->nu;
     if (out != sino) {
         cudaError_t e = cudaMemcpyAsync(out, sino, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
@@ -355,6 +361,7 @@ int pyronn_sim_motion_blur(pyronn_geom_t g, const void *sino, void *out, const f
     if (length < 1 || length > 1024) return set_error(PYRONN_INVALID_ARG, "kernel length %d out of [1, 1024]", length);
     if (sino == out) return set_error(PYRONN_INVALID_ARG, "motion blur cannot run in place");
     const long long n = (long long)batch * g->n_views * g->nv * g->nu;
+    if ((rc = ensure_device(g))) return rc;
     return cuda_rc(launch_sim_blur(sino, out, angles, length, g->nu, g->nv, g->n_views, n, dtype, stream), "blur launch");
 }
 
@@ -365,6 +372,7 @@ int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch
     if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
     if (weight != PYRONN_BP_PLAIN && weight != PYRONN_BP_INV_W2)
         return set_error(PYRONN_INVALID_ARG, "unknown back-projection weight %d", weight);
+    if ((rc = ensure_device(g))) return rc;
     OpParams p = make_params(g, batch);
     p.weight = weight;
     if (g->bp_variant == 1) return cuda_rc(launch_bp(p, sino, vol, dtype, stream), "back-projection launch");
@@ -379,6 +387,7 @@ int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype,
     if ((rc = check_ptr(vol, "vol")) || (rc = check_ptr(sino, "sino"))) return rc;
     if (weight != PYRONN_BP_PLAIN && weight != PYRONN_BP_INV_W2)
         return set_error(PYRONN_INVALID_ARG, "unknown back-projection weight %d", weight);
+    if ((rc = ensure_device(g))) return rc;
     OpParams p = make_params(g, batch);
     p.weight = weight;
     float *acc = nullptr;
@@ -394,6 +403,7 @@ static int host_op(pyronn_geom_t g, const void *in_host, void *out_host, int dty
     int rc = common_checks(g, dtype, batch);
     if (rc) return rc;
     if (!in_host || !out_host) return set_error(PYRONN_INVALID_ARG, "null host buffer");
+    if ((rc = ensure_device(g))) return rc;
     size_t es = dtype_size(dtype);
     size_t vol_bytes = es * (size_t)g->nx * g->ny * g->nz * batch;
     size_t sino_bytes = es * (size_t)g->nu * g->nv * g->n_views * batch;

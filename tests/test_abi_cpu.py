@@ -151,3 +151,26 @@ def test_fp_config_invariants(L, dtype_size, dtype):
     assert g2.fp_config(td)["kernel"] == 2
     g2.set_variant(0, 1)
     assert g2.fp_config(td)["kernel"] == 1
+
+
+def test_argument_checks_precede_the_device(L):
+    """Every entry point rejects bad arguments before touching the device (these run without a GPU):
+    empty batches, volumes too large for 32-bit indexing, unknown filters, non-finite steps, jitter
+    axes and in-place use, blur lengths, ring view ranges."""
+    from paper_2511_08427_gb300.operators import Geometry
+    g = Geometry.cone_circular((4, 5, 6), (1, 1, 1), (3, 4), (1, 1), 3, 1.0, 10.0, 20.0)
+    a, b = ctypes.c_void_p(256), ctypes.c_void_p(512)
+    h = g.handle
+    assert L.pyronn_fp(h, a, b, 0, 0, None) == -1                       # batch 0
+    assert b"batch" in L.pyronn_last_error()
+    big = Geometry.cone_circular((1024, 2048, 1024), (1, 1, 1), (4, 4), (1, 1), 2, 1.0, 5000.0, 9000.0)
+    assert L.pyronn_adjoint(big.handle, a, b, 0, 1, None) == -1          # 2^31 voxels
+    assert b"too large" in L.pyronn_last_error()
+    assert L.pyronn_fbp_filter(h, a, b, 7, 0, 1, None) == -1             # unknown filter
+    assert L.pyronn_adjoint_update(h, a, None, float("nan"), b, 0, 1, None) == -1
+    assert L.pyronn_sim_detector_jitter(h, a, b, a, 2, 0, 1, None) == -1  # axis
+    assert L.pyronn_sim_detector_jitter(h, a, a, b, 0, 0, 1, None) == -1  # in place
+    assert L.pyronn_sim_motion_blur(h, a, b, a, 0, 0, 1, None) == -1      # length 0
+    assert L.pyronn_sim_ring(h, a, b, a, a, 1, 2, 9, 0, 1, None) == -1    # views [2, 9) of 3
+    assert L.pyronn_sim_gaussian_noise(h, a, b, None, 0.0, 1.0, 0, 1, None) == -1
+    assert L.pyronn_fp(h, ctypes.c_void_p(8), b, 0, 1, None) == -3        # misaligned
