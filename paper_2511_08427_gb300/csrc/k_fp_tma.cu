@@ -68,14 +68,6 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *map
         : "memory");
 }
 
-// floor and fraction of q in [-2^22, 2^22): q + 1.5 * 2^23 rounded down is an integer
-__device__ __forceinline__ void floor_frac(float q, int &i, float &f) {
-    const float M = 12582912.0f;
-    float t = __fadd_rd(q, M);
-    i = __float_as_int(t) - 0x4B400000;
-    f = q - (t - M);
-}
-
 struct TmaMaps {
     CUtensorMap map[3];   // one box shape per march axis
 };
@@ -266,6 +258,9 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 const T *box = bi ? buf1 : buf0;
                 const int sy = BXb, sz = BXb * BYb;
                 const int limit = box_elems - (sz + sy + 1);
+                // floor(q) + 2^23 + 2^22 is the bit pattern of q + 1.5 2^23 rounded down, so the box offset
+                // sum floor(q_a) stride_a comes straight from the three bit patterns (unsigned wrap-around)
+                const unsigned boff = 0x4B400000u * (unsigned)(sz + sy + 1);
                 // position relative to the box origin: q = c0 + kf * step
                 const float c0x = fmaf(hdt, r.dx, r.cx - (float)sb.lo[0]);
                 const float c0y = fmaf(hdt, r.dy, r.cy - (float)sb.lo[1]);
@@ -279,12 +274,11 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 float v100 = 0.0f, v101 = 0.0f, v110 = 0.0f, v111 = 0.0f;
                 for (int k = ka; k <= kb; ++k, kf += 1.0f) {
                     const float qx = fmaf(kf, stx, c0x), qy = fmaf(kf, sty, c0y), qz = fmaf(kf, stz, c0z);
-                    int ix, iy, iz;
-                    float ax, ay, az;
-                    floor_frac(qx, ix, ax);
-                    floor_frac(qy, iy, ay);
-                    floor_frac(qz, iz, az);
-                    const int base = iz * sz + iy * sy + ix;
+                    const float M = 12582912.0f;
+                    const float tx = __fadd_rd(qx, M), ty = __fadd_rd(qy, M), tz = __fadd_rd(qz, M);
+                    const float ax = qx - (tx - M), ay = qy - (ty - M), az = qz - (tz - M);
+                    const int base = (int)((unsigned)__float_as_int(tz) * (unsigned)sz +
+                                           ((unsigned)__float_as_int(ty) * (unsigned)sy + ((unsigned)__float_as_int(tx) - boff)));
                     if ((unsigned)base > (unsigned)limit) {
                         atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
                         acc += trilerp_zero(vb, p.vol, qx + (float)sb.lo[0], qy + (float)sb.lo[1],
