@@ -355,6 +355,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
     // per-ray state kept across slabs: value y dt (0: nothing to scatter), and the global FP32 ray's
     // march-axis coordinate, inverse step and sample range, which define the slab partition
     float yv[AS_RPT], rcm[AS_RPT], rinv[AS_RPT];
+    float rdir[AS_RPT][6];   // unit direction d and its change dd from the tile's corner ray (slab-independent)
     int rk0[AS_RPT], rk1[AS_RPT];
     unsigned ybits = 0u;
 #pragma unroll
@@ -398,6 +399,12 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         rcm[j] = cm;
         rinv[j] = 1.0f / (dt * dm);
         rk0[j] = k0;
+        {
+            float d[3], dd[3];
+            as_ray_dir(sh.tile, (float)(u - tu0), (float)(v - tv0), d, dd);
+            rdir[j][0] = d[0]; rdir[j][1] = d[1]; rdir[j][2] = d[2];
+            rdir[j][3] = dd[0]; rdir[j][4] = dd[1]; rdir[j][5] = dd[2];
+        }
         rk1[j] = k1;
         const float qa = fmaf(fmaf((float)k0, dt, 0.5f * dt), dm, cm);
         const float qb = fmaf(fmaf((float)k1, dt, 0.5f * dt), dm, cm);
@@ -522,8 +529,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
             // precise local ray: point P on the plane through X_s, unit direction d, and the offset e
             // of (X_s + P) . d from the phase T dt of the tile's corner ray (K + f = T)
             const float fu = (float)(u - tu0), fv = (float)(v - tv0);
-            float d[3], dd[3];
-            as_ray_dir(sh.tile, fu, fv, d, dd);
+            const float d[3] = {rdir[j][0], rdir[j][1], rdir[j][2]};
+            const float dd[3] = {rdir[j][3], rdir[j][4], rdir[j][5]};
             const float P0 = fmaf(fv, S.Ev[0], fmaf(fu, S.Eu[0], S.A[0]));
             const float P1 = fmaf(fv, S.Ev[1], fmaf(fu, S.Eu[1], S.A[1]));
             const float P2 = fmaf(fv, S.Ev[2], fmaf(fu, S.Eu[2], S.A[2]));
@@ -541,7 +548,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                 // int32 boxes: every sample adds its eight corner weights, no cell bookkeeping; the
                 // samples ka..kb are visited from ka + r cyclically
                 const int n = kb - ka + 1;
-                const int r = rot % n;
+                const int r = rot < n ? rot : rot % n;
                 const int wrap = n - r;
                 float jj = jf + (float)r;
                 for (int ii = 0; ii < n; ++ii, jj += 1.0f) {
