@@ -657,21 +657,19 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
             for (int gi = tid; gi < ngroups; gi += AS_NT) {
                 float4 *pb = reinterpret_cast<float4 *>(box) + gi;
                 float4 q = *pb;
-                bool nz;
-                if (fx) {
-                    const int4 qi = *reinterpret_cast<const int4 *>(&q);
-                    nz = (qi.x | qi.y | qi.z | qi.w) != 0;
-                    q = make_float4(__int2float_rn(qi.x) * isc, __int2float_rn(qi.y) * isc,
-                                    __int2float_rn(qi.z) * isc, __int2float_rn(qi.w) * isc);
-                } else {
-                    // a group summing to -0 is left as is: adding to -0 is exact
-                    nz = q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f;
-                }
+                const int4 qi = *reinterpret_cast<const int4 *>(&q);
+                // FP32 boxes: a group summing to -0 is left as is (adding to -0 is exact)
+                const bool nz = fx ? (qi.x | qi.y | qi.z | qi.w) != 0
+                                   : (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f);
                 if (nz) {
                     *pb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (fx)
+                        q = make_float4(__int2float_rn(qi.x) * isc, __int2float_rn(qi.y) * isc,
+                                        __int2float_rn(qi.z) * isc, __int2float_rn(qi.w) * isc);
                     const int gx = lo0 + 4 * xg, gy = lo1 + ly, gz = lo2 + lz;
                     if ((unsigned)gy < (unsigned)p.vol.ny && (unsigned)gz < (unsigned)p.vol.nz) {
-                        float *dst = vb + ((long long)gz * p.vol.ny + gy) * p.vol.nx + gx;
+                        // 32-bit index: volumes hold fewer than 2^31 voxels (gx may be slightly negative)
+                        float *dst = vb + ((gz * p.vol.ny + gy) * p.vol.nx + gx);
                         if (vec4 && gx >= 0 && gx + 3 < p.vol.nx) {
                             asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(q.x),
                                          "f"(q.y), "f"(q.z), "f"(q.w)
