@@ -379,6 +379,25 @@ def run_gpu(args):
         gd_ms[name] = e0.elapsed_time(e1) / max(2, K // 2)
     del p_meas, x_it
 
+    def time_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # BF16 storage (FP32 arithmetic) forward projection of the same workload, and the FBP filter
+    vol_bf, sino_bf = vol.bfloat16(), torch.empty(sino.shape, device=dev, dtype=torch.bfloat16)
+    fp_bf16_ms = time_ms(lambda: ops.forward_project(vol_bf, g, out=sino_bf), max(3, K // 2))
+    del vol_bf, sino_bf
+    fbp_out = torch.empty_like(sino)
+    fbp_ms = time_ms(lambda: ops.fbp_filter(sino, g, out=fbp_out), max(3, K // 2))
+    del fbp_out
+
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     import ctypes
     h_vol = torch.from_numpy(vol_np).pin_memory()
@@ -448,6 +467,8 @@ def run_gpu(args):
         "bp_gupdates_per_s": bp_rate, "fwd_adj_ms_per_iter": (fp_sum + adj_sum) / K,
         "kernel_ms": {"fp": fp_sum / K, "adjoint": adj_sum / K, "bp": bp_sum / K},
         "gd_iteration_ms": gd_ms,
+        "fp_bf16": {"ms": fp_bf16_ms, "gsamples_per_s": n_samples / (fp_bf16_ms * 1e-3) / 1e9},
+        "fbp_filter_ms": fbp_ms,
         "samples_per_fp": n_samples, "updates_per_bp": n_updates,
         "e2e": {"value": e2e_rate, "unit": "G ray-samples/s", "h2d_bytes_per_step": int(vol_np.nbytes),
                 "d2h_bytes_per_step": int(h_sino.numel() * 4), "call": "pyronn_fp_host"},
