@@ -84,7 +84,7 @@ template <typename T>
 __device__ __forceinline__ float bilerp0(const T *__restrict__ q, int nu, int nv, int iu, int iv, float au, float av) {
     const bool u0 = (unsigned)iu < (unsigned)nu, u1 = (unsigned)(iu + 1) < (unsigned)nu;
     const bool v0 = (unsigned)iv < (unsigned)nv, v1 = (unsigned)(iv + 1) < (unsigned)nv;
-    const long long base = (long long)iv * nu + iu;
+    const int base = iv * nu + iu;   // one view holds fewer than 2^31 pixels
     const float q00 = (v0 && u0) ? ldg_f32(q + base) : 0.0f;
     const float q01 = (v0 && u1) ? ldg_f32(q + base + 1) : 0.0f;
     const float q10 = (v1 && u0) ? ldg_f32(q + base + nu) : 0.0f;
@@ -138,12 +138,24 @@ __device__ __forceinline__ void bp_brick(const OpParams &p, const T *__restrict_
                 magic_floor(fmaf(na, iw, V.fu), iu, au);
                 iu += V.U0;
                 const float om = W2 ? iw * iw : 1.0f;
+                // the column iu and its bounds are shared by the brick's z voxels (32-bit detector
+                // indices: one view holds fewer than 2^31 pixels)
+                const bool u0 = (unsigned)iu < (unsigned)nu, u1 = (unsigned)(iu + 1) < (unsigned)nu;
 #pragma unroll
                 for (int z = 0; z < BZ; ++z) {
                     int iv;
                     float av;
                     magic_floor(fmaf(nb, iw, V.fv), iv, av);
-                    acc[z] = fmaf(om, bilerp0(q, nu, nv, iu, iv + V.V0, au, av), acc[z]);
+                    iv += V.V0;
+                    const bool v0 = (unsigned)iv < (unsigned)nv, v1 = (unsigned)(iv + 1) < (unsigned)nv;
+                    const T *r = q + (iv * nu + iu);
+                    const float q00 = (v0 && u0) ? ldg_f32(r) : 0.0f;
+                    const float q01 = (v0 && u1) ? ldg_f32(r + 1) : 0.0f;
+                    const float q10 = (v1 && u0) ? ldg_f32(r + nu) : 0.0f;
+                    const float q11 = (v1 && u1) ? ldg_f32(r + nu + 1) : 0.0f;
+                    const float r0 = fmaf(au, q01 - q00, q00);
+                    const float r1 = fmaf(au, q11 - q10, q10);
+                    acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
                     nb += V.Qb[2];
                 }
             } else {
