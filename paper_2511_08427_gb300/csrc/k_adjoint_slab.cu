@@ -25,7 +25,9 @@
 // GPU, integer reductions a single operation (about 3.6x the throughput). Where a bound allows, a
 // slab's box therefore holds int32 fixed-point sums: every cell contribution c (an FP32 register
 // sum) enters as round(c 2^e), and the box value is converted back with 2^-e when it is added to
-// the volume. The scale 2^e is chosen per (tile, slab) so that no box value can exceed 2^30:
+// the volume. The scale 2^e is chosen per (tile, slab) so that no single contribution exceeds 2^22
+// (M 2^e < 2^22, which lets one FFMA with 1.5 2^23 do the rounding, see below) and no box value can
+// exceed 2^30:
 //   |box value| <= M * R * (1 / delta + 1)
 // with M = max |y| dt over the tile, delta the index-space distance between consecutive samples
 // (>= dt / max spacing; the sampled sum of the trilinear hat along one line is at most 1 / delta + 1
@@ -33,8 +35,12 @@
 // voxel's support (-1, 1)^3: such a ray meets the plane through the voxel's centre inside the
 // rectangle of half-widths 1 + |slope| of the tile's rays, and the pixels mapping there are counted
 // through the tile's pixel-to-plane Jacobian on the slab's two end planes (10 % slack for the
-// projective variation across a tile). Slabs whose bound R (1 / delta + 1) exceeds 128 (dense rays:
-// the quantum would exceed M 2^-23) keep FP32 reductions.
+// projective variation across a tile). Slabs whose bound H = R (1 / delta + 1) exceeds 128 (dense
+// rays) keep FP32 reductions; below it the contribution bound is the binding one, so the quantum 2^-e
+// lies in (2^-22 M, 2^-21 M] and each contribution is off by at most half of it.
+// A contribution c with |c| <= 2^22 is rounded to the nearest integer (ties to even) by
+// t = fma(w, a, 1.5 2^23), whose bits are 0x4B400000 + round(c): one full-rate FFMA and an integer
+// add instead of a product and a conversion.
 #include <algorithm>
 #include <atomic>
 #include <mutex>
@@ -90,6 +96,12 @@ __device__ __forceinline__ void as_red_shared(unsigned addr, float v) {
 
 __device__ __forceinline__ void as_red_shared_s32(unsigned addr, int v) {
     asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+// round(w a) (ties to even) for |w a| <= 2^22: the bits of w a + 1.5 2^23, formed by one FFMA with a
+// single rounding, are 0x4B400000 + round(w a)
+__device__ __forceinline__ int as_fix(float w, float a) {
+    return (int)(__float_as_uint(fmaf(w, a, 12582912.0f)) - 0x4B400000u);
 }
 
 // Floor and fraction without the range clamp, for positions inside a slab box (|q| far below 2^22);
@@ -454,6 +466,9 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         lo[0] = lo[0] >= 0 ? (lo[0] & ~3) : -(((-lo[0]) + 3) & ~3);
         int e0 = hi[0] - lo[0] + 1;
         e0 = (e0 + 3) & ~3;
+        // x-march tiles: lanes sit on different rows at nearly the same x, so rows of an odd number of
+        // 16-byte groups put any 8 consecutive rows on 8 different bank groups
+        if (m == 0 && ((e0 >> 2) & 1) == 0) e0 += 4;
         const int e1 = hi[1] - lo[1] + 1, e2 = hi[2] - lo[2] + 1;
         const bool fits = e0 > 0 && e1 > 0 && e2 > 0 && (long long)e0 * e1 * e2 <= box_cap;
         for (int a = 0; a < 3; ++a) S.lo[a] = lo[a];
@@ -469,7 +484,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                 const float smax = (float)fmax(p.sx, fmax(p.sy, p.sz));
                 const float H = R * (smax / dt + 1.0f);
                 float sc, isc;
-                if (H <= 128.0f && as_fixed_scale(__uint_as_float(sh.ymax) * H, sc, isc)) {
+                // bound max(H, 2^8) M: box values below 2^30, single contributions below 2^22
+                if (H <= 128.0f && as_fixed_scale(__uint_as_float(sh.ymax) * fmaxf(H, 256.0f), sc, isc)) {
                     S.scale = sc;
                     S.inv_scale = isc;
                     atomicAdd(&sh.nfixed, 1);
@@ -549,6 +565,54 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                 // samples ka..kb are visited from ka + r cyclically
                 const int n = kb - ka + 1;
                 const int r = rot < n ? rot : rot % n;
+                // Positions are monotone in the sample index along each axis (each is a chain of
+                // correctly rounded FMAs of it), so when the first and the last sample's 2 x 2 x 2 blocks
+                // lie in the box, every sample's does, and the segment needs no per-sample test. The
+                // comparisons fail for NaN, which takes the checked loop.
+                const float s_a = fmaf(jf, dt, c_r), s_b = fmaf(jf + (float)(n - 1), dt, c_r);
+                const float pa0 = fmaf(s_a, qd0, qP0), pb0 = fmaf(s_b, qd0, qP0);
+                const float pa1 = fmaf(s_a, qd1, qP1), pb1 = fmaf(s_b, qd1, qP1);
+                const float pa2 = fmaf(s_a, qd2, qP2), pb2 = fmaf(s_b, qd2, qP2);
+                const float ex0 = (float)(Ex - 1), ex1 = (float)(Ey - 1), ex2 = (float)(Ez - 1);
+                if (pa0 >= 0.f && pb0 >= 0.f && pa0 < ex0 && pb0 < ex0 && pa1 >= 0.f && pb1 >= 0.f && pa1 < ex1 &&
+                    pb1 < ex1 && pa2 >= 0.f && pb2 >= 0.f && pa2 < ex2 && pb2 < ex2) {
+                    // floor(q) = bits(q + 1.5 2^23 rounded down) - 0x4B400000 for 0 <= q < 2^22; the
+                    // constant is folded into the box base address (unsigned arithmetic mod 2^32)
+                    const float Mg = 12582912.0f;
+                    const unsigned abase = box_base - 0x4B400000u * (sz4 + sy4 + 4u);
+                    auto sample = [&](float jj) {
+                        const float sj = fmaf(jj, dt, c_r);
+                        const float q0 = fmaf(sj, qd0, qP0), q1 = fmaf(sj, qd1, qP1), q2 = fmaf(sj, qd2, qP2);
+                        const float t0 = __fadd_rd(q0, Mg), t1 = __fadd_rd(q1, Mg), t2 = __fadd_rd(q2, Mg);
+                        const float ax = q0 - (t0 - Mg), ay = q1 - (t1 - Mg), az = q2 - (t2 - Mg);
+                        const unsigned a = abase + 4u * __float_as_uint(t0) + sy4 * __float_as_uint(t1) +
+                                           sz4 * __float_as_uint(t2);
+                        const float wz1 = ys * az, wz0 = ys - wz1;
+                        const float oay = 1.f - ay, oax = 1.f - ax;
+                        const float w00 = wz0 * oay, w01 = wz0 * ay, w10 = wz1 * oay, w11 = wz1 * ay;
+                        as_red_shared_s32(a, as_fix(w00, oax));
+                        as_red_shared_s32(a + 4u, as_fix(w00, ax));
+                        as_red_shared_s32(a + sy4, as_fix(w01, oax));
+                        as_red_shared_s32(a + sy4 + 4u, as_fix(w01, ax));
+                        as_red_shared_s32(a + sz4, as_fix(w10, oax));
+                        as_red_shared_s32(a + sz4 + 4u, as_fix(w10, ax));
+                        as_red_shared_s32(a + sz4 + sy4, as_fix(w11, oax));
+                        as_red_shared_s32(a + sz4 + sy4 + 4u, as_fix(w11, ax));
+                    };
+                    // one loop of n steps for every lane (lanes of a warp stay in step whatever their
+                    // rotation): local index jj = jf + r + ii, wrapped back by n past jf + n - 1; two
+                    // independent samples per step
+                    const float nf = (float)n, jw = jf + nf;
+                    float jj = jf + (float)r;
+                    int ii = 0;
+                    for (; ii + 1 < n; ii += 2, jj += 2.0f) {
+                        const float j1 = jj + 1.0f;
+                        sample(jj >= jw ? jj - nf : jj);
+                        sample(j1 >= jw ? j1 - nf : j1);
+                    }
+                    if (ii < n) sample(jj >= jw ? jj - nf : jj);
+                    continue;
+                }
                 const int wrap = n - r;
                 float jj = jf + (float)r;
                 for (int ii = 0; ii < n; ++ii, jj += 1.0f) {
@@ -788,6 +852,7 @@ long long as_tile_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0
                 e[a] = std::min<long long>(e[a], dims[a] + 2 * G + 2);
             }
             e[0] = ((e[0] + 3 + 3) / 4) * 4;   // x start rounded down (<= 3 more), extent rounded up
+            if ((e[0] / 4) % 2 == 0) e[0] += 4;  // odd number of 16-byte groups per row (x-march tiles)
             best = std::max(best, e[0] * e[1] * e[2]);
         }
     }

@@ -272,20 +272,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 int pbase = -1;
                 float v000 = 0.0f, v001 = 0.0f, v010 = 0.0f, v011 = 0.0f;
                 float v100 = 0.0f, v101 = 0.0f, v110 = 0.0f, v111 = 0.0f;
-                for (int k = ka; k <= kb; ++k, kf += 1.0f) {
-                    const float qx = fmaf(kf, stx, c0x), qy = fmaf(kf, sty, c0y), qz = fmaf(kf, stz, c0z);
-                    const float M = 12582912.0f;
-                    const float tx = __fadd_rd(qx, M), ty = __fadd_rd(qy, M), tz = __fadd_rd(qz, M);
-                    const float ax = qx - (tx - M), ay = qy - (ty - M), az = qz - (tz - M);
-                    const int base = (int)((unsigned)__float_as_int(tz) * (unsigned)sz +
-                                           ((unsigned)__float_as_int(ty) * (unsigned)sy + ((unsigned)__float_as_int(tx) - boff)));
-                    if ((unsigned)base > (unsigned)limit) {
-                        atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
-                        acc += trilerp_zero(vb, p.vol, qx + (float)sb.lo[0], qy + (float)sb.lo[1],
-                                            qz + (float)sb.lo[2]);
-                        pbase = -1;
-                        continue;
-                    }
+                const float M = 12582912.0f;
+                auto sample = [&](int base, float ax, float ay, float az) {
                     if (base != pbase) {
                         const T *s0 = box + base;
                         v000 = to_f32(s0[0]); v001 = to_f32(s0[1]);
@@ -301,6 +289,39 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                     const float c0 = fmaf(ay, c01 - c00, c00);
                     const float c1 = fmaf(ay, c11 - c10, c10);
                     acc += fmaf(az, c1 - c0, c0);
+                };
+                // Positions are one correctly rounded FMA of the sample index, hence monotone in it along
+                // each axis: when the first and the last sample's cells lie in the box (index in
+                // [0, extent - 2] on every axis), all of them do and the loop needs no per-sample test.
+                // The comparisons fail for NaN, which takes the checked loop.
+                const float qax = fmaf(kf, stx, c0x), qbx = fmaf((float)kb, stx, c0x);
+                const float qay = fmaf(kf, sty, c0y), qby = fmaf((float)kb, sty, c0y);
+                const float qaz = fmaf(kf, stz, c0z), qbz = fmaf((float)kb, stz, c0z);
+                const float ex = (float)(BXb - 1), ey = (float)(BYb - 1), ez = (float)(BZb - 1);
+                if (qax >= 0.f && qbx >= 0.f && qax < ex && qbx < ex && qay >= 0.f && qby >= 0.f && qay < ey &&
+                    qby < ey && qaz >= 0.f && qbz >= 0.f && qaz < ez && qbz < ez) {
+                    for (int k = ka; k <= kb; ++k, kf += 1.0f) {
+                        const float qx = fmaf(kf, stx, c0x), qy = fmaf(kf, sty, c0y), qz = fmaf(kf, stz, c0z);
+                        const float tx = __fadd_rd(qx, M), ty = __fadd_rd(qy, M), tz = __fadd_rd(qz, M);
+                        const int base = (int)((unsigned)__float_as_int(tz) * (unsigned)sz +
+                                               ((unsigned)__float_as_int(ty) * (unsigned)sy + ((unsigned)__float_as_int(tx) - boff)));
+                        sample(base, qx - (tx - M), qy - (ty - M), qz - (tz - M));
+                    }
+                } else {
+                    for (int k = ka; k <= kb; ++k, kf += 1.0f) {
+                        const float qx = fmaf(kf, stx, c0x), qy = fmaf(kf, sty, c0y), qz = fmaf(kf, stz, c0z);
+                        const float tx = __fadd_rd(qx, M), ty = __fadd_rd(qy, M), tz = __fadd_rd(qz, M);
+                        const int base = (int)((unsigned)__float_as_int(tz) * (unsigned)sz +
+                                               ((unsigned)__float_as_int(ty) * (unsigned)sy + ((unsigned)__float_as_int(tx) - boff)));
+                        if ((unsigned)base > (unsigned)limit) {
+                            atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
+                            acc += trilerp_zero(vb, p.vol, qx + (float)sb.lo[0], qy + (float)sb.lo[1],
+                                                qz + (float)sb.lo[2]);
+                            pbase = -1;
+                            continue;
+                        }
+                        sample(base, qx - (tx - M), qy - (ty - M), qz - (tz - M));
+                    }
                 }
             } else {
                 if (tid == 0) atomicAdd(p.flags + FLAG_SLAB_OVERFLOW, 1);
