@@ -15,11 +15,11 @@
 // where the tile's corner ray meets the plane through X_s, the per-pixel steps of that point, and
 // the lattice phase of the corner ray at X_s. Each ray then needs only small FP32 quantities.
 //
-// Lanes of a warp take the 32 pixels of one tile row. Where the tile marches along x, every lane sits
-// at nearly the same x index at a given step, so with 16-byte row pitches all lanes would hit one word
-// of each 16-byte bank group; there each group of 8 lanes walks its slab samples starting 3 samples
-// later than the previous group (cyclically), which spreads the reductions over the banks. Integer
-// additions commute exactly, so the order does not change fixed-point results.
+// Lanes of a warp take the 32 pixels of one tile row, so at a given step their samples lie along one
+// line across the march direction. Where the tile marches along y or z that line runs along x: the
+// lanes hit consecutive words of one box row, i.e. different banks. Where it marches along x, the lanes
+// sit on different rows at nearly the same x; the box rows then get an odd pitch (one word more than
+// the x extent, a multiple of four), which puts 32 consecutive rows on 32 different banks.
 //
 // Box accumulation: shared-memory FP32 reductions are a load / compare-and-swap sequence on this
 // GPU, integer reductions a single operation (about 3.6x the throughput). Where a bound allows, a
@@ -68,6 +68,7 @@ struct AsSlab {                 // per (tile, slab), relative to the box centre 
     float f;                    // phase of the corner ray at X_s: (X_s - C) . dref = (K + f) dt
     int K;
     int lo[3], ext[3];          // box origin and extents (voxels); ext[0] == 0: empty slab
+    int px;                     // row pitch of the box (words): ext[0], or ext[0] + 1 on x-march tiles
     float scale, inv_scale;     // fixed-point scale 2^e and 2^-e; scale == 0: FP32 box
 };
 
@@ -363,7 +364,6 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
     const int nslab_all = (Nm + 1 - base0 + D - 1) / D;
 
     // rays of this thread: tile row warp * AS_RPT + j, lanes along u
-    const int rot = m == 0 ? 3 * (lane >> 3) : 0;   // sample-order rotation (bank spreading)
     // per-ray state kept across slabs: value y dt (0: nothing to scatter), and the global FP32 ray's
     // march-axis coordinate, inverse step and sample range, which define the slab partition
     float yv[AS_RPT], rcm[AS_RPT], rinv[AS_RPT];
@@ -466,13 +466,14 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         lo[0] = lo[0] >= 0 ? (lo[0] & ~3) : -(((-lo[0]) + 3) & ~3);
         int e0 = hi[0] - lo[0] + 1;
         e0 = (e0 + 3) & ~3;
-        // x-march tiles: lanes sit on different rows at nearly the same x, so rows of an odd number of
-        // 16-byte groups put any 8 consecutive rows on 8 different bank groups
-        if (m == 0 && ((e0 >> 2) & 1) == 0) e0 += 4;
+        // x-march tiles: the lanes of a warp sit on different rows at nearly the same x, so the rows get
+        // an odd pitch, which puts 32 consecutive rows on 32 different banks
+        const int px = m == 0 ? e0 + 1 : e0;
         const int e1 = hi[1] - lo[1] + 1, e2 = hi[2] - lo[2] + 1;
-        const bool fits = e0 > 0 && e1 > 0 && e2 > 0 && (long long)e0 * e1 * e2 <= box_cap;
+        const bool fits = e0 > 0 && e1 > 0 && e2 > 0 && (long long)px * e1 * e2 <= box_cap;
         for (int a = 0; a < 3; ++a) S.lo[a] = lo[a];
         S.ext[0] = fits ? e0 : 0;
+        S.px = px;
         S.ext[1] = e1;
         S.ext[2] = e2;
         S.scale = 0.0f;
@@ -517,7 +518,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         const float ysc = fx ? S.scale : 1.0f;
         const bool per_sample = fx && !cell_fixed;
         const int lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2];
-        const unsigned sy4 = 4u * (unsigned)Ex, sz4 = 4u * (unsigned)(Ex * Ey);
+        const int Px = S.px;
+        const unsigned sy4 = 4u * (unsigned)Px, sz4 = 4u * (unsigned)(Px * Ey);
         const int b_lo = base0 + s * D;
         const int b_hi = min(b_lo + D, Nm);
 #pragma unroll 1
@@ -561,10 +563,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
             const float qd0 = d[0] * isx, qd1 = d[1] * isy, qd2 = d[2] * isz;
             const float ys = y * ysc;   // fixed point: y dt 2^e; FP32 boxes: y dt
             if (per_sample) {
-                // int32 boxes: every sample adds its eight corner weights, no cell bookkeeping; the
-                // samples ka..kb are visited from ka + r cyclically
+                // int32 boxes: every sample adds its eight corner weights, no cell bookkeeping
                 const int n = kb - ka + 1;
-                const int r = rot < n ? rot : rot % n;
                 // Positions are monotone in the sample index along each axis (each is a chain of
                 // correctly rounded FMAs of it), so when the first and the last sample's 2 x 2 x 2 blocks
                 // lie in the box, every sample's does, and the segment needs no per-sample test. The
@@ -599,24 +599,18 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                         as_red_shared_s32(a + sz4 + sy4, as_fix(w11, oax));
                         as_red_shared_s32(a + sz4 + sy4 + 4u, as_fix(w11, ax));
                     };
-                    // one loop of n steps for every lane (lanes of a warp stay in step whatever their
-                    // rotation): local index jj = jf + r + ii, wrapped back by n past jf + n - 1; two
-                    // independent samples per step
-                    const float nf = (float)n, jw = jf + nf;
-                    float jj = jf + (float)r;
+                    // two independent samples per step
+                    float jj = jf;
                     int ii = 0;
                     for (; ii + 1 < n; ii += 2, jj += 2.0f) {
-                        const float j1 = jj + 1.0f;
-                        sample(jj >= jw ? jj - nf : jj);
-                        sample(j1 >= jw ? j1 - nf : j1);
+                        sample(jj);
+                        sample(jj + 1.0f);
                     }
-                    if (ii < n) sample(jj >= jw ? jj - nf : jj);
+                    if (ii < n) sample(jj);
                     continue;
                 }
-                const int wrap = n - r;
-                float jj = jf + (float)r;
+                float jj = jf;
                 for (int ii = 0; ii < n; ++ii, jj += 1.0f) {
-                    if (ii == wrap) jj -= (float)n;
                     const float sj = fmaf(jj, dt, c_r);
                     int ix, iy, iz;
                     float ax, ay, az;
@@ -628,7 +622,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                     const float w00 = wz0 * oay, w01 = wz0 * ay, w10 = wz1 * oay, w11 = wz1 * ay;
                     if ((unsigned)ix < (unsigned)(Ex - 1) && (unsigned)iy < (unsigned)(Ey - 1) &&
                         (unsigned)iz < (unsigned)(Ez - 1)) {
-                        const unsigned a = box_base + 4u * (unsigned)((iz * Ey + iy) * Ex + ix);
+                        const unsigned a = box_base + 4u * (unsigned)((iz * Ey + iy) * Px + ix);
                         as_red_shared_s32(a, __float2int_rn(w00 * oax));
                         as_red_shared_s32(a + 4u, __float2int_rn(w00 * ax));
                         as_red_shared_s32(a + sy4, __float2int_rn(w01 * oax));
@@ -664,7 +658,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                             (unsigned)piz < (unsigned)(Ez - 1)) {
                             // the cell's 2 x 2 x 2 block lies in the box: eight reductions (corners outside the
                             // volume land in the box margin and are dropped when the box is added)
-                            const unsigned a = box_base + 4u * (unsigned)((piz * Ey + piy) * Ex + pix);
+                            const unsigned a = box_base + 4u * (unsigned)((piz * Ey + piy) * Px + pix);
                             if (fx) {
                                 as_red_shared_s32(a, __float2int_rn(a0));
                                 as_red_shared_s32(a + 4u, __float2int_rn(a1v));
@@ -708,9 +702,11 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
             }
         }
         __syncthreads();
-        // add the box to the volume (float4 groups along x, all-zero groups skipped) and zero it again;
-        // group indices advance by AS_NT groups per step without divisions
+        // add the box to the volume (groups of four voxels along x, float4 reductions, all-zero groups
+        // skipped) and zero it again; group indices advance by AS_NT groups per step without divisions.
+        // Rows of odd pitch are read and cleared word by word.
         if (Ex > 0) {
+            const bool vbox = (Px & 3) == 0;
             const int gx4 = Ex >> 2;
             const int ngroups = gx4 * Ey * Ez;
             const int srow = AS_NT / gx4;
@@ -719,14 +715,18 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
             const int row0 = tid / gx4;
             int ly = row0 % Ey, lz = row0 / Ey;
             for (int gi = tid; gi < ngroups; gi += AS_NT) {
-                float4 *pb = reinterpret_cast<float4 *>(box) + gi;
-                float4 q = *pb;
+                float *pw = box + (4 * xg + Px * (ly + Ey * lz));
+                float4 q = vbox ? *reinterpret_cast<const float4 *>(pw) : make_float4(pw[0], pw[1], pw[2], pw[3]);
                 const int4 qi = *reinterpret_cast<const int4 *>(&q);
                 // FP32 boxes: a group summing to -0 is left as is (adding to -0 is exact)
                 const bool nz = fx ? (qi.x | qi.y | qi.z | qi.w) != 0
                                    : (q.x != 0.f || q.y != 0.f || q.z != 0.f || q.w != 0.f);
                 if (nz) {
-                    *pb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (vbox) {
+                        *reinterpret_cast<float4 *>(pw) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        pw[0] = 0.f; pw[1] = 0.f; pw[2] = 0.f; pw[3] = 0.f;
+                    }
                     if (fx)
                         q = make_float4(__int2float_rn(qi.x) * isc, __int2float_rn(qi.y) * isc,
                                         __int2float_rn(qi.z) * isc, __int2float_rn(qi.w) * isc);
@@ -852,7 +852,7 @@ long long as_tile_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0
                 e[a] = std::min<long long>(e[a], dims[a] + 2 * G + 2);
             }
             e[0] = ((e[0] + 3 + 3) / 4) * 4;   // x start rounded down (<= 3 more), extent rounded up
-            if ((e[0] / 4) % 2 == 0) e[0] += 4;  // odd number of 16-byte groups per row (x-march tiles)
+            if (m == 0) e[0] += 1;                 // odd row pitch of x-march boxes
             best = std::max(best, e[0] * e[1] * e[2]);
         }
     }
@@ -883,8 +883,9 @@ static long long as_bound(const pyronn_geom *g, int depth, int guard) {
     return best.load();
 }
 
-// Deepest slab (8, 6 or 4 planes, and at most AS_MAX_SLABS slabs per tile) whose box fits in ~100 KB,
-// so that two CTAs share an SM; otherwise the shallowest that fits in 160 KB.
+// Deepest slab (8, 6 or 4 planes, and at most AS_MAX_SLABS slabs per tile) whose box lets two CTAs
+// share an SM (228 KB of shared memory per SM, 1 KB reserved per CTA, the static tile state);
+// otherwise the shallowest that fits in 160 KB.
 AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     AdjSlabCfg c{};
     if (g->ndim != 3) return c;
@@ -892,7 +893,8 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     const int dmin = (nmax + 2 + AS_MAX_SLABS - 1) / AS_MAX_SLABS;
     const double smin = std::min(g->sx, std::min(g->sy, g->sz));
     c.guard = 1 + (int)std::floor(g->dt / smin);
-    const long long soft = (100 * 1024) / 4, hard = (160 * 1024) / 4;
+    const long long soft = ((228 * 1024) / 2 - 1024 - (long long)sizeof(AsShared) - 64) / 4;
+    const long long hard = (160 * 1024) / 4;
     long long need = 0;
     for (int d : {8, 6, 4}) {
         const int depth = std::max(d, dmin);
@@ -929,6 +931,9 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
     const size_t smem = sizeof(float) * (size_t)c.box_cap;
     e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return (int)e;
     const int per_launch = 65535 / p.n_views > 0 ? 65535 / p.n_views : 1;
     for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
         const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
@@ -945,6 +950,9 @@ template <typename T>
 static int launch_slab_batched_t(const PlanLaunch &L, int grid, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(adjoint_slab_batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(adjoint_slab_batched_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     for (int i = 0; i < L.n; ++i) {
         e = cudaMemsetAsync(L.v[i].acc, 0, sizeof(float) * (size_t)L.v[i].p.vol_elems, st);
@@ -978,6 +986,9 @@ int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t
 int adjoint_slab_batched_occupancy(size_t smem, int *blocks_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(adjoint_slab_batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(adjoint_slab_batched_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adjoint_slab_batched_kernel<float>, AS_NT,
                                                               smem);
