@@ -454,6 +454,9 @@ def run_gpu(args):
     rl_bp = alu_roofline("bp_brick_kernel", "paper_2511_08427_gb300/csrc/k_bp_brick.cu",
                          n_updates * BP_FLOP_PER_UPDATE, bp_s)
     rl_bp["flop_per_update"] = BP_FLOP_PER_UPDATE
+    # kernels of one step: FP (plus the y-fastest copy it stages x-march slabs from), adjoint, BP
+    fpc = g.fp_config()
+    launches_per_step = 3 + (1 if fpc["kernel"] == 3 and fpc["y_fastest_x_march"] else 0)
     # the dominant kernel of the step (longest average launch)
     dominant = max((rl_fp, rl_adj, rl_bp), key=lambda r: r["launch_ms"])
 
@@ -472,7 +475,7 @@ def run_gpu(args):
         "samples_per_fp": n_samples, "updates_per_bp": n_updates,
         "e2e": {"value": e2e_rate, "unit": "G ray-samples/s", "h2d_bytes_per_step": int(vol_np.nbytes),
                 "d2h_bytes_per_step": int(h_sino.numel() * 4), "call": "pyronn_fp_host"},
-        "gpu_launches": 3 * K,
+        "gpu_launches": launches_per_step * K,
         "clocks": clk,
         "roofline": dominant,
         "rooflines": {"fp": rl_fp, "adjoint": rl_adj, "bp": rl_bp},

@@ -154,7 +154,8 @@ PYRONN_API int pyronn_geom_count_samples(pyronn_geom_t g, int64_t *total);
  * ---------------------------------------------------------------------------------------- */
 
 /* Forward projection (Sec. 2.1 ray-driven; operator A of Sec. 2.2): sino = A vol, overwriting
- * sino. */
+ * sino. The TMA-staged projector may first copy the volume into a geometry-owned y-fastest buffer
+ * (allocated on first use; see PYRONN_TUNE_FP_TRANSPOSE). */
 PYRONN_API int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, void *stream);
 
 /* Matched adjoint (operator A^T of Sec. 2.2, the exact transpose of pyronn_fp):
@@ -244,16 +245,19 @@ PYRONN_API int pyronn_adjoint_noalloc(pyronn_geom_t g, const void *sino, void *v
  * operator (the paper's layers carry a batch dimension, Listing 1; here every batch member may
  * have its own geometry). Each CTA takes (view, detector tile) items (forward projection) or
  * volume-brick items (adjoint, back-projection) from a device work counter, largest items first.
- * Every call is one cudaMemsetAsync of the counter plus one kernel launch on `stream` and
- * allocates nothing, so calls can be captured in a CUDA graph; the plan is created (and the
- * geometries' device tables uploaded) before capture.
+ * Every call is one cudaMemsetAsync of the counter plus one kernel launch on `stream` (the forward
+ * projection first adds one transpose launch per volume staged from a y-fastest copy) and allocates
+ * nothing, so calls can be captured in a CUDA graph; the plan is created (and the geometries'
+ * device tables uploaded) before capture.
  * ---------------------------------------------------------------------------------------- */
 typedef struct pyronn_plan *pyronn_plan_t;
 
 /* n (1..16) 3D geometries; dtype is the storage type of every buffer used with the plan. Volumes
  * whose rows (Nx elements) are not a multiple of 16 bytes cannot use tensor copies: their forward
- * projection runs as a separate per-geometry launch on the same stream. The plan refers to the
- * geometries (it does not own them): keep them alive while the plan is used. */
+ * projection runs as a separate per-geometry launch on the same stream. The plan allocates a
+ * y-fastest copy buffer for every volume whose forward projection stages x-march boxes from one
+ * (PYRONN_TUNE_FP_TRANSPOSE of its geometry at creation). The plan refers to the geometries (it
+ * does not own them): keep them alive while the plan is used. */
 PYRONN_API int pyronn_plan_create(int n, const pyronn_geom_t *geoms, int dtype, pyronn_plan_t *out);
 PYRONN_API int pyronn_plan_destroy(pyronn_plan_t plan);
 
@@ -297,18 +301,23 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * 2 shared-memory slab buffers (2 overlaps the next copy with sampling; 1 halves shared memory so
  * more CTAs fit on an SM); PYRONN_TUNE_ADJ_ACCUM: accumulation of the slab-ordered adjoint's
  * shared-memory boxes, 0 automatic (int32 fixed point with a power-of-two scale per tile and slab
- * wherever a bound on the box values keeps the quantum at or below 2^-23 of the tile's largest
- * contribution, FP32 reductions elsewhere; fixed-point boxes take one reduction per sample and
- * corner), 1 FP32 reductions only, 2 as 0 but fixed-point boxes take one reduction per corner of
+ * wherever a bound on the box values allows it, with a quantum between 2^-22 and 2^-21 of the
+ * tile's largest |y| dt, FP32 reductions elsewhere; fixed-point boxes take one reduction per sample
+ * and corner), 1 FP32 reductions only, 2 as 0 but fixed-point boxes take one reduction per corner of
  * each cell a ray passes (weights summed in registers while the ray stays in the cell);
  * PYRONN_TUNE_FP_CTAS_PER_SM: CTAs per SM the TMA-staged forward projector is compiled for, 2 or
  * 4 (4 caps registers at 64 per thread; automatic: 4 where four CTAs' slab buffers fit in shared
- * memory). */
+ * memory); PYRONN_TUNE_FP_TRANSPOSE: 0 (automatic) lets the TMA-staged forward projector stage the
+ * slabs of detector tiles that march along x from a y-fastest copy of the volume, made on the
+ * call's stream into a geometry-owned buffer of the volume's size (allocated on first use), so that
+ * the rays of a warp, which spread across y there, read consecutive shared-memory words; 1 stages
+ * every slab from the volume itself. */
 typedef enum {
     PYRONN_TUNE_FP_DEPTH = 0,
     PYRONN_TUNE_FP_BUFFERS = 1,
     PYRONN_TUNE_ADJ_ACCUM = 2,
-    PYRONN_TUNE_FP_CTAS_PER_SM = 3
+    PYRONN_TUNE_FP_CTAS_PER_SM = 3,
+    PYRONN_TUNE_FP_TRANSPOSE = 4
 } pyronn_tuning_param;
 PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
 
@@ -326,11 +335,12 @@ PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
 PYRONN_API int pyronn_geom_read_flags(pyronn_geom_t g, int *out, int reset);
 
 /* Forward-projector configuration that would be used for element type dtype (host computation,
- * no GPU needed), 16 ints: [0] kernel (1 direct, 2 slab thread-staged, 3 slab TMA-staged, 4 texture
+ * no GPU needed), 20 ints: [0] kernel (1 direct, 2 slab thread-staged, 3 slab TMA-staged, 4 texture
  * gather),
  * [1] slab depth, [2] guard planes, [3] first slab plane, [4..12] TMA box (x, y, z) for march
  * axes x, y, z, [13] elements per TMA buffer, [14] dynamic shared memory bytes per CTA,
- * [15] thread-staged box capacity (elements). */
+ * [15] thread-staged box capacity (elements), [16] 1 if x-march boxes are staged from the y-fastest
+ * copy of the volume (their innermost TMA axis is then y), [17..19] zero. */
 PYRONN_API int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out);
 
 /* Matched-adjoint configuration (host computation, no GPU needed), 4 ints: [0] kernel (1 atomic

@@ -467,8 +467,9 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         int e0 = hi[0] - lo[0] + 1;
         e0 = (e0 + 3) & ~3;
         // x-march tiles: the lanes of a warp sit on different rows at nearly the same x, so the rows get
-        // an odd pitch, which puts 32 consecutive rows on 32 different banks
-        const int px = m == 0 ? e0 + 1 : e0;
+        // an odd pitch (where the configuration's box budget allows), which puts 32 consecutive rows on
+        // 32 different banks
+        const int px = m == 0 && cfg.xpad ? e0 + 1 : e0;
         const int e1 = hi[1] - lo[1] + 1, e2 = hi[2] - lo[2] + 1;
         const bool fits = e0 > 0 && e1 > 0 && e2 > 0 && (long long)px * e1 * e2 <= box_cap;
         for (int a = 0; a < 3; ++a) S.lo[a] = lo[a];
@@ -818,7 +819,7 @@ namespace {
 // Largest box (floats) of one 32 x 32 tile over its first and last slab (the box extent is convex in
 // the slab position). Margins follow the kernel: lo = floor(min) - 1, hi = floor(max) + 2, x start
 // rounded down to 4 and x extent up to 4, +1 for FP32 rounding.
-long long as_tile_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0, int D, int G) {
+long long as_tile_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0, int D, int G, int xpad) {
     const int tu1 = std::min(tu0 + AS_TU, g->nu) - 1, tv1 = std::min(tv0 + AS_TV, g->nv) - 1;
     RayD cr[4];
     for (int c = 0; c < 4; ++c) cr[c] = ray_setup_d(rec, g, (c & 1) ? tu1 : tu0, (c & 2) ? tv1 : tv0);
@@ -852,7 +853,7 @@ long long as_tile_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0
                 e[a] = std::min<long long>(e[a], dims[a] + 2 * G + 2);
             }
             e[0] = ((e[0] + 3 + 3) / 4) * 4;   // x start rounded down (<= 3 more), extent rounded up
-            if (m == 0) e[0] += 1;                 // odd row pitch of x-march boxes
+            if (m == 0 && xpad) e[0] += 1;         // odd row pitch of x-march boxes
             best = std::max(best, e[0] * e[1] * e[2]);
         }
     }
@@ -861,7 +862,7 @@ long long as_tile_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0
 
 }  // namespace
 
-static long long as_bound(const pyronn_geom *g, int depth, int guard) {
+static long long as_bound(const pyronn_geom *g, int depth, int guard, int xpad) {
     const int ntu = (g->nu + AS_TU - 1) / AS_TU, ntv = (g->nv + AS_TV - 1) / AS_TV;
     std::atomic<int> next(0);
     std::atomic<long long> best(0);
@@ -870,7 +871,7 @@ static long long as_bound(const pyronn_geom *g, int depth, int guard) {
         for (int n = next.fetch_add(1); n < g->n_views; n = next.fetch_add(1))
             for (int j = 0; j < ntv; ++j)
                 for (int i = 0; i < ntu; ++i)
-                    local = std::max(local, as_tile_bound(g, g->fp_rec[n], i * AS_TU, j * AS_TV, depth, guard));
+                    local = std::max(local, as_tile_bound(g, g->fp_rec[n], i * AS_TU, j * AS_TV, depth, guard, xpad));
         long long cur = best.load();
         while (local > cur && !best.compare_exchange_weak(cur, local)) {
         }
@@ -884,8 +885,9 @@ static long long as_bound(const pyronn_geom *g, int depth, int guard) {
 }
 
 // Deepest slab (8, 6 or 4 planes, and at most AS_MAX_SLABS slabs per tile) whose box lets two CTAs
-// share an SM (228 KB of shared memory per SM, 1 KB reserved per CTA, the static tile state);
-// otherwise the shallowest that fits in 160 KB.
+// share an SM (224 KB of shared memory, 1 KB reserved per CTA, the static tile state), first
+// with the odd row pitch of x-march boxes, then without it; otherwise the shallowest that fits in
+// 160 KB (16-byte pitch).
 AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     AdjSlabCfg c{};
     if (g->ndim != 3) return c;
@@ -893,15 +895,23 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     const int dmin = (nmax + 2 + AS_MAX_SLABS - 1) / AS_MAX_SLABS;
     const double smin = std::min(g->sx, std::min(g->sy, g->sz));
     c.guard = 1 + (int)std::floor(g->dt / smin);
-    const long long soft = ((228 * 1024) / 2 - 1024 - (long long)sizeof(AsShared) - 64) / 4;
+    // two CTAs per SM: 224 KB of the SM's shared memory, 1 KB reserved per CTA, the static tile
+    // state (the occupancy calculator on GB300 admits two CTAs of 114264 bytes each, not of 115152)
+    const long long soft = ((224 * 1024) / 2 - 1024 - (long long)sizeof(AsShared) - 64) / 4;
     const long long hard = (160 * 1024) / 4;
     long long need = 0;
-    for (int d : {8, 6, 4}) {
-        const int depth = std::max(d, dmin);
-        need = as_bound(g, depth, c.guard);
-        c.depth = depth;
-        if (need <= soft) break;
-    }
+    bool fit = false;
+    for (int xpad = 1; xpad >= 0 && !fit; --xpad)
+        for (int d : {8, 6, 4}) {
+            const int depth = std::max(d, dmin);
+            need = as_bound(g, depth, c.guard, xpad);
+            c.depth = depth;
+            c.xpad = xpad;
+            if (need <= soft) {
+                fit = true;
+                break;
+            }
+        }
     c.box_cap = (int)std::min(need, hard);
     c.valid = need > 0 && need <= hard;
     c.allow_fixed = g->tuning.adj_accum != 1;

@@ -12,6 +12,14 @@
 // Sample loop: positions relative to the box origin, floor / fraction by the round-down
 // magic-number addition (no conversion-pipe instructions), eight shared-memory reads, seven
 // lerps, one accumulate.
+//
+// Box layout: the rays of a warp (16 x 2 pixels) spread across the tile's march axis. Where the
+// tile marches along y or z they spread along x, the innermost axis of the volume, and read
+// consecutive shared-memory words. Where it marches along x they would sit on different rows at
+// nearly the same x, all on one word of each 16-byte bank group; there the slabs are staged from a
+// y-fastest copy of the volume (made per call by a tiled transpose), so that y is the box's
+// innermost axis. The sample loop works in the box's memory order (first, second, z) = (x, y, z)
+// or (y, x, z).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -150,6 +158,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
     const int box_elems = BXb * BYb * BZb;
     const unsigned box_bytes = (unsigned)(sizeof(T) * box_elems);
     const CUtensorMap *tmap = &maps3[m];
+    // x-march tile staged from the y-fastest copy: the box's memory order is (y, x, z)
+    const bool yt = m == 0 && cfg.xt;
 
     // slab range of this tile: union of the rays' in-box sample ranges
     if (hit) {
@@ -198,10 +208,12 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
         const int lx = m == 0 ? lom : lo1, hx = m == 0 ? him : hi1;
         const int ly = m == 0 ? lo1 : (m == 1 ? lom : lo2), hy = m == 0 ? hi1 : (m == 1 ? him : hi2);
         const int lz = m == 2 ? lom : lo2, hz = m == 2 ? him : hi2;
-        // TMA: the innermost start coordinate must be 16-byte aligned
-        const int x0 = lx >= 0 ? (lx / align) * align : -(((-lx) + align - 1) / align) * align;
-        sb.lo[0] = x0; sb.lo[1] = ly; sb.lo[2] = lz;
-        sb.fits = (hx - x0 + 1 <= BXb) && (hy - ly + 1 <= BYb) && (hz - lz + 1 <= BZb);
+        // TMA: the innermost start coordinate (x, or y for the y-fastest copy) must be 16-byte aligned
+        const int li = yt ? ly : lx;
+        const int i0 = li >= 0 ? (li / align) * align : -(((-li) + align - 1) / align) * align;
+        const int x0 = yt ? lx : i0, y0 = yt ? i0 : ly;
+        sb.lo[0] = x0; sb.lo[1] = y0; sb.lo[2] = lz;
+        sb.fits = (hx - x0 + 1 <= BXb) && (hy - y0 + 1 <= BYb) && (hz - lz + 1 <= BZb);
         return sb;
     };
 
@@ -212,7 +224,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
             const SlabBox sb0 = slab_box(s_first);
             sh.box[0] = sb0;
             mbar_expect_tx(bars[0], box_bytes);
-            tma_load_4d(smem_u32(buf0), tmap, bars[0], sb0.lo[0], sb0.lo[1], sb0.lo[2], b);
+            tma_load_4d(smem_u32(buf0), tmap, bars[0], yt ? sb0.lo[1] : sb0.lo[0], yt ? sb0.lo[0] : sb0.lo[1],
+                        sb0.lo[2], b);
         }
         for (int i = 0; i < nsl; ++i) {
             const int s = s_first + i;
@@ -223,7 +236,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 sh.box[(i + 1) & 1] = sbn;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(bars[bi ^ 1], box_bytes);
-                tma_load_4d(smem_u32(bi ? buf0 : buf1), tmap, bars[bi ^ 1], sbn.lo[0], sbn.lo[1], sbn.lo[2], b);
+                tma_load_4d(smem_u32(bi ? buf0 : buf1), tmap, bars[bi ^ 1], yt ? sbn.lo[1] : sbn.lo[0],
+                            yt ? sbn.lo[0] : sbn.lo[1], sbn.lo[2], b);
             }
             // a copy lost anywhere aborts every CTA at its next slab, so the launch ends promptly (the
             // flag is read before the wait so that the two latencies overlap)
@@ -256,16 +270,21 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
             }
             if (sb.fits) {
                 const T *box = bi ? buf1 : buf0;
-                const int sy = BXb, sz = BXb * BYb;
+                // memory order of the box: (first, second, z) = (x, y, z), or (y, x, z) when yt; the
+                // loop's "x" and "y" below are the first and second axes
+                const int BF = yt ? BYb : BXb, BS = yt ? BXb : BYb;
+                const int sy = BF, sz = BF * BS;
                 const int limit = box_elems - (sz + sy + 1);
                 // floor(q) + 2^23 + 2^22 is the bit pattern of q + 1.5 2^23 rounded down, so the box offset
                 // sum floor(q_a) stride_a comes straight from the three bit patterns (unsigned wrap-around)
                 const unsigned boff = 0x4B400000u * (unsigned)(sz + sy + 1);
                 // position relative to the box origin: q = c0 + kf * step
-                const float c0x = fmaf(hdt, r.dx, r.cx - (float)sb.lo[0]);
-                const float c0y = fmaf(hdt, r.dy, r.cy - (float)sb.lo[1]);
+                const float rcf = yt ? r.cy : r.cx, rdf = yt ? r.dy : r.dx;
+                const float rcs = yt ? r.cx : r.cy, rds = yt ? r.dx : r.dy;
+                const float c0x = fmaf(hdt, rdf, rcf - (float)(yt ? sb.lo[1] : sb.lo[0]));
+                const float c0y = fmaf(hdt, rds, rcs - (float)(yt ? sb.lo[0] : sb.lo[1]));
                 const float c0z = fmaf(hdt, r.dz, r.cz - (float)sb.lo[2]);
-                const float stx = p.dt * r.dx, sty = p.dt * r.dy, stz = p.dt * r.dz;
+                const float stx = p.dt * rdf, sty = p.dt * rds, stz = p.dt * r.dz;
                 float kf = (float)ka;
                 // the eight corner values stay in registers while consecutive samples share a cell;
                 // lanes that keep their cell issue no shared-memory reads
@@ -297,7 +316,7 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 const float qax = fmaf(kf, stx, c0x), qbx = fmaf((float)kb, stx, c0x);
                 const float qay = fmaf(kf, sty, c0y), qby = fmaf((float)kb, sty, c0y);
                 const float qaz = fmaf(kf, stz, c0z), qbz = fmaf((float)kb, stz, c0z);
-                const float ex = (float)(BXb - 1), ey = (float)(BYb - 1), ez = (float)(BZb - 1);
+                const float ex = (float)(BF - 1), ey = (float)(BS - 1), ez = (float)(BZb - 1);
                 if (qax >= 0.f && qbx >= 0.f && qax < ex && qbx < ex && qay >= 0.f && qby >= 0.f && qay < ey &&
                     qby < ey && qaz >= 0.f && qbz >= 0.f && qaz < ez && qbz < ez) {
                     for (int k = ka; k <= kb; ++k, kf += 1.0f) {
@@ -315,8 +334,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                                                ((unsigned)__float_as_int(ty) * (unsigned)sy + ((unsigned)__float_as_int(tx) - boff)));
                         if ((unsigned)base > (unsigned)limit) {
                             atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
-                            acc += trilerp_zero(vb, p.vol, qx + (float)sb.lo[0], qy + (float)sb.lo[1],
-                                                qz + (float)sb.lo[2]);
+                            acc += trilerp_zero(vb, p.vol, (yt ? qy : qx) + (float)sb.lo[0],
+                                                (yt ? qx : qy) + (float)sb.lo[1], qz + (float)sb.lo[2]);
                             pbase = -1;
                             continue;
                         }
@@ -336,7 +355,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 sh.box[(i + 1) & 1] = sbn;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(bars[0], box_bytes);
-                tma_load_4d(smem_u32(buf0), tmap, bars[0], sbn.lo[0], sbn.lo[1], sbn.lo[2], b);
+                tma_load_4d(smem_u32(buf0), tmap, bars[0], yt ? sbn.lo[1] : sbn.lo[0], yt ? sbn.lo[0] : sbn.lo[1],
+                            sbn.lo[2], b);
             }
         }
     }
@@ -419,6 +439,29 @@ __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_batched_kernel(const __gr
     }
 }
 
+// y-fastest copy of nvol volumes (x fastest): out[v][z][x][y] = in[v][z][y][x], through 32 x 32 tiles
+// in shared memory so that both the reads and the writes are coalesced. blockIdx.z strides over the
+// nz * nvol (z, volume) slices.
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_xy_kernel(const T *__restrict__ in, T *__restrict__ out, int nx,
+                                                           int ny, long long nslices) {
+    __shared__ T tile[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    for (long long sl = blockIdx.z; sl < nslices; sl += gridDim.z) {
+        const long long base = sl * nx * ny;
+        __syncthreads();   // the previous slice's tile has been written out
+        for (int j = threadIdx.y; j < 32; j += 8) {
+            const int x = x0 + threadIdx.x, y = y0 + j;
+            if (x < nx && y < ny) tile[j][threadIdx.x] = in[base + (long long)y * nx + x];
+        }
+        __syncthreads();
+        for (int j = threadIdx.y; j < 32; j += 8) {
+            const int y = y0 + threadIdx.x, x = x0 + j;
+            if (x < nx && y < ny) out[base + (long long)x * ny + y] = tile[threadIdx.x][j];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // host: box bound per march axis, tensor map, launch
 // ---------------------------------------------------------------------------------------------
@@ -478,11 +521,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 // Box dimensions for the TMA kernel, or depth = 0 if it cannot be used (shared memory too small or
-// the row pitch is not a multiple of 16 bytes).
-FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf, int minb) {
+// the row pitch is not a multiple of 16 bytes). xt: x-march boxes may come from a y-fastest copy of
+// the volume (taken where its rows, ny elements, are a multiple of 16 bytes too).
+FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf, int minb, int xt) {
     FpTmaBox c{};
     const int align = 16 / (int)elem;
     if (((size_t)g->nx * elem) % 16 != 0) return c;
+    c.xt = xt && ((size_t)g->ny * elem) % 16 == 0;
     // slab depth: a multiple of the x alignment so that x-march boxes start aligned
     c.depth = depth > 0 ? ((depth + align - 1) / align) * align : 8;
     c.nbuf = nbuf == 2 ? 2 : 1;   // default: one buffer (more CTAs per SM beat the copy overlap)
@@ -519,13 +564,19 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
             else e[a] = (int)ext[m][a];
             if (a != m && e[a] == 0) e[a] = 1;   // axis never chosen: keep a valid box
         }
-        // x is the innermost TMA dimension: round up, plus room for the aligned start unless the slab
-        // planes themselves start aligned (march along x)
-        e[0] = m == 0 ? ((e[0] + align - 1) / align) * align : ((e[0] + 2 * (align - 1)) / align) * align;
-        // march along x: all rays of a warp sit at nearly the same x, so a row pitch that is a multiple
-        // of 32 bytes would fold their rows onto 4 or fewer bank groups; an odd multiple of 16 bytes
-        // spreads consecutive rows over 8
-        if (m == 0 && (e[0] * (int)elem) % 32 == 0) e[0] += align;
+        if (m == 0 && c.xt) {
+            // y-fastest copy: y is the innermost TMA dimension (room for the aligned start); the
+            // rays of a warp read consecutive words of a row
+            e[1] = ((e[1] + 2 * (align - 1)) / align) * align;
+        } else {
+            // x is the innermost TMA dimension: round up, plus room for the aligned start unless the
+            // slab planes themselves start aligned (march along x)
+            e[0] = m == 0 ? ((e[0] + align - 1) / align) * align : ((e[0] + 2 * (align - 1)) / align) * align;
+            // march along x: all rays of a warp sit at nearly the same x, so a row pitch that is a
+            // multiple of 32 bytes would fold their rows onto 4 or fewer bank groups; an odd multiple
+            // of 16 bytes spreads consecutive rows over 8
+            if (m == 0 && (e[0] * (int)elem) % 32 == 0) e[0] += align;
+        }
         for (int a = 0; a < 3; ++a) e[a] = std::min(e[a], 256);
         c.bx[m] = e[0]; c.by[m] = e[1]; c.bz[m] = e[2];
         maxel = std::max(maxel, e[0] * e[1] * e[2]);
@@ -540,13 +591,41 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
     return c;
 }
 
+// Tensor maps of nb consecutive volumes (1 in plans) for the three march axes; with cfg.xt the x-march map
+// covers the y-fastest copy vt.
 template <typename T>
-static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, cudaStream_t st) {
+static int encode_maps(const OpParams &p, const FpTmaBox &cfg, const void *vol, const void *vt, int nb,
+                       CUtensorMap maps[3]) {
+    if (cfg.xt && !vt) return (int)cudaErrorInvalidValue;
     auto enc = encode_fn();
     if (!enc) return (int)cudaErrorNotSupported;
     const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    const int nx = p.vol.nx, ny = p.vol.ny, nz = p.vol.nz;
+    cuuint64_t gdim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nb};
+    cuuint64_t gstride[3] = {(cuuint64_t)nx * sizeof(T), (cuuint64_t)nx * ny * sizeof(T),
+                             (cuuint64_t)nx * ny * nz * sizeof(T)};
+    cuuint32_t estride[4] = {1, 1, 1, 1};
+    cuuint64_t gdim_t[4] = {(cuuint64_t)ny, (cuuint64_t)nx, (cuuint64_t)nz, (cuuint64_t)nb};
+    cuuint64_t gstride_t[3] = {(cuuint64_t)ny * sizeof(T), (cuuint64_t)nx * ny * sizeof(T),
+                               (cuuint64_t)nx * ny * nz * sizeof(T)};
+    for (int m = 0; m < 3; ++m) {
+        const bool t = m == 0 && cfg.xt;
+        cuuint32_t box[4] = {(cuuint32_t)(t ? cfg.by[m] : cfg.bx[m]), (cuuint32_t)(t ? cfg.bx[m] : cfg.by[m]),
+                             (cuuint32_t)cfg.bz[m], 1};
+        CUresult r = enc(&maps[m], dt, 4, const_cast<void *>(t ? vt : vol), t ? gdim_t : gdim, t ? gstride_t : gstride,
+                         box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
+    }
+    return 0;
+}
+
+template <typename T>
+static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *vol_t, void *sino,
+                        cudaStream_t st) {
+    if (cfg.xt && !vol_t) return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)cfg.nbuf * sizeof(T) * (size_t)cfg.buf_elems + 128;
     auto kern = cfg.minb == 4 ? fp_tma_kernel<T, 4> : fp_tma_kernel<T, 2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -558,45 +637,20 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
     for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
         const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
         const T *vptr = (const T *)vol + b0 * p.vol_elems;
+        T *tptr = cfg.xt ? (T *)vol_t + b0 * p.vol_elems : nullptr;
+        if (cfg.xt) {
+            const long long nsl = (long long)nz * nb;
+            dim3 tg(ceil_div(nx, 32), ceil_div(ny, 32), (unsigned)std::min<long long>(nsl, 65535));
+            transpose_xy_kernel<T><<<tg, dim3(32, 8), 0, st>>>(vptr, tptr, nx, ny, nsl);
+        }
         TmaMaps maps;
         std::memset(&maps, 0, sizeof(maps));
-        cuuint64_t gdim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nb};
-        cuuint64_t gstride[3] = {(cuuint64_t)nx * sizeof(T), (cuuint64_t)nx * ny * sizeof(T),
-                                 (cuuint64_t)nx * ny * nz * sizeof(T)};
-        cuuint32_t estride[4] = {1, 1, 1, 1};
-        for (int m = 0; m < 3; ++m) {
-            cuuint32_t box[4] = {(cuuint32_t)cfg.bx[m], (cuuint32_t)cfg.by[m], (cuuint32_t)cfg.bz[m], 1};
-            CUresult r = enc(&maps.map[m], dt, 4, (void *)vptr, gdim, gstride, box, estride,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
-        }
+        const int rc = encode_maps<T>(p, cfg, vptr, tptr, nb, maps.map);
+        if (rc) return rc;
         dim3 grid(ceil_div(p.det.nu, TMA_TU), ceil_div(p.det.nv, TMA_TV), p.n_views * nb);
         kern<<<grid, TMA_NT, smem, st>>>(p, cfg, maps, vptr, (T *)sino + b0 * p.sino_elems);
     }
     return (int)cudaGetLastError();
-}
-
-template <typename T>
-static int encode_maps(const OpParams &p, const FpTmaBox &cfg, const void *vol, int nb, CUtensorMap maps[3]) {
-    auto enc = encode_fn();
-    if (!enc) return (int)cudaErrorNotSupported;
-    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                   : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
-    const int nx = p.vol.nx, ny = p.vol.ny, nz = p.vol.nz;
-    cuuint64_t gdim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nb};
-    cuuint64_t gstride[3] = {(cuuint64_t)nx * sizeof(T), (cuuint64_t)nx * ny * sizeof(T),
-                             (cuuint64_t)nx * ny * nz * sizeof(T)};
-    cuuint32_t estride[4] = {1, 1, 1, 1};
-    for (int m = 0; m < 3; ++m) {
-        cuuint32_t box[4] = {(cuuint32_t)cfg.bx[m], (cuuint32_t)cfg.by[m], (cuuint32_t)cfg.bz[m], 1};
-        CUresult r = enc(&maps[m], dt, 4, const_cast<void *>(vol), gdim, gstride, box, estride,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
-    }
-    return 0;
 }
 
 // the persistent kernel is compiled for four CTAs per SM (64 registers) where four CTAs' buffers fit
@@ -612,7 +666,14 @@ static int launch_batched_t(const PlanLaunch &L, int grid, size_t smem, cudaStre
     PlanMaps M;
     std::memset(&M, 0, sizeof(M));
     for (int i = 0; i < L.n; ++i) {
-        int rc = encode_maps<T>(L.v[i].p, L.v[i].cfg, L.v[i].in, 1, M.map[i]);
+        const PlanVolume &V = L.v[i];
+        if (V.cfg.xt) {
+            if (!V.vt) return (int)cudaErrorInvalidValue;
+            const int nx = V.p.vol.nx, ny = V.p.vol.ny;
+            dim3 tg(ceil_div(nx, 32), ceil_div(ny, 32), (unsigned)std::min(V.p.vol.nz, 65535));
+            transpose_xy_kernel<T><<<tg, dim3(32, 8), 0, st>>>((const T *)V.in, (T *)V.vt, nx, ny, V.p.vol.nz);
+        }
+        int rc = encode_maps<T>(V.p, V.cfg, V.in, V.vt, 1, M.map[i]);
         if (rc) return rc;
     }
     e = cudaMemsetAsync(L.counter, 0, sizeof(int), st);
@@ -650,12 +711,13 @@ int fp_tma_batched_occupancy(int dtype, size_t smem, int *blocks_per_sm) {
     }
 }
 
-int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream) {
+int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *vol_t, void *sino, int dtype,
+                  void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     switch (dtype) {
-        case PYRONN_F32: return launch_tma_t<float>(p, cfg, vol, sino, st);
-        case PYRONN_BF16: return launch_tma_t<__nv_bfloat16>(p, cfg, vol, sino, st);
-        case PYRONN_F16: return launch_tma_t<__half>(p, cfg, vol, sino, st);
+        case PYRONN_F32: return launch_tma_t<float>(p, cfg, vol, vol_t, sino, st);
+        case PYRONN_BF16: return launch_tma_t<__nv_bfloat16>(p, cfg, vol, vol_t, sino, st);
+        case PYRONN_F16: return launch_tma_t<__half>(p, cfg, vol, vol_t, sino, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -108,7 +108,8 @@ const AdjSlabCfg &adj_cfg(pyronn_geom_t g) { return geom_adj_cfg(g); }
 const FpTmaBox &tma_cfg(pyronn_geom_t g, int dtype) {
     std::lock_guard<std::mutex> lk(g->mu);
     if (!g->tma_ready[dtype]) {
-        g->tma_cfg[dtype] = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf, g->tuning.fp_minb);
+        g->tma_cfg[dtype] = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf,
+                                              g->tuning.fp_minb, g->tuning.fp_transpose == 0);
         g->tma_ready[dtype] = 1;
     }
     return g->tma_cfg[dtype];
@@ -133,7 +134,13 @@ int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch
     }
     if (g->fp_variant == 0 || g->fp_variant == 3 || g->fp_variant == 4) {
         const FpTmaBox &tb = tma_cfg(g, dtype);
-        if (tb.depth > 0) return cuda_rc(launch_fp_tma(p, tb, vol, sino, dtype, stream), "forward projection launch");
+        if (tb.depth > 0) {
+            if (tb.xt) {
+                const size_t bytes = dtype_size(dtype) * (size_t)p.vol_elems * (size_t)batch;
+                if ((rc = ensure_buffer(g, &g->d_vol_t, &g->vol_t_bytes, bytes, "transposed volume"))) return rc;
+            }
+            return cuda_rc(launch_fp_tma(p, tb, vol, g->d_vol_t, sino, dtype, stream), "forward projection launch");
+        }
     }
     return cuda_rc(launch_fp(p, fp_cfg(g), vol, sino, dtype, stream), "forward projection launch");
 }
@@ -142,7 +149,7 @@ int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out) {
     clear_error();
     if (!g || !out) return set_error(PYRONN_INVALID_ARG, "null argument");
     if (dtype_size(dtype) == 0) return set_error(PYRONN_UNSUPPORTED_DTYPE, "unsupported dtype %d", dtype);
-    for (int i = 0; i < 16; ++i) out[i] = 0;
+    for (int i = 0; i < 20; ++i) out[i] = 0;
     const FpTmaBox &tb = tma_cfg(g, dtype);
     const FpSlabCfg &sc = fp_cfg(g);
     int kernel = 1;
@@ -163,6 +170,7 @@ int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out) {
     out[14] = kernel == 3 ? (int)((size_t)tb.nbuf * dtype_size(dtype) * (size_t)tb.buf_elems + 128)
                           : (kernel == 2 ? (int)(sizeof(float) * (size_t)sc.smem_floats) : 0);
     out[15] = sc.smem_floats;
+    out[16] = kernel == 3 ? tb.xt : 0;
     return PYRONN_OK;
 }
 
@@ -196,6 +204,10 @@ int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
             if (value != 0 && value != 2 && value != 4)
                 return set_error(PYRONN_INVALID_ARG, "CTAs per SM must be 0 (automatic), 2 or 4 (got %d)", value);
             g->tuning.fp_minb = value;
+            break;
+        case PYRONN_TUNE_FP_TRANSPOSE:
+            if (value < 0 || value > 1) return set_error(PYRONN_INVALID_ARG, "transpose mode %d out of [0, 1]", value);
+            g->tuning.fp_transpose = value;
             break;
         case PYRONN_TUNE_ADJ_ACCUM:
             if (value < 0 || value > 2) return set_error(PYRONN_INVALID_ARG, "accumulation mode %d out of [0, 2]", value);

@@ -28,6 +28,8 @@ struct pyronn_plan {
     std::vector<AdjSlabCfg> acfg;
     float *d_acc = nullptr;             // FP32 accumulation volumes (BF16 / FP16 plans)
     std::vector<size_t> acc_off;
+    unsigned char *d_vt = nullptr;      // y-fastest copies of the volumes whose x-march FP boxes use one
+    std::vector<size_t> vt_off;         // byte offsets into d_vt (per geometry; unused without a copy)
 };
 
 namespace {
@@ -58,7 +60,8 @@ int pyronn_plan_create(int n, const pyronn_geom_t *geoms, int dtype, pyronn_plan
         else if ((rc = ensure_device(g)) == PYRONN_OK) {
             // volumes whose rows are not a multiple of 16 bytes (depth 0) cannot use tensor copies; the
             // forward projection runs them through the per-geometry projector on the same stream
-            FpTmaBox c = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf, g->tuning.fp_minb);
+            FpTmaBox c = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf,
+                                           g->tuning.fp_minb, g->tuning.fp_transpose == 0);
             P->geoms.push_back(g);
             P->cfg.push_back(c);
         }
@@ -140,9 +143,26 @@ int pyronn_plan_create(int n, const pyronn_geom_t *geoms, int dtype, pyronn_plan
             }
         }
     }
+    // y-fastest copies for the forward projector (256-byte aligned, one per volume that uses one)
+    size_t vt_total = 0;
+    for (int i = 0; i < n; ++i) {
+        P->vt_off.push_back(vt_total);
+        const pyronn_geom *g = P->geoms[i];
+        if (P->cfg[i].depth > 0 && P->cfg[i].xt)
+            vt_total += (dtype_size(dtype) * (size_t)g->nx * g->ny * g->nz + 255) / 256 * 256;
+    }
+    if (vt_total > 0) {
+        e = cudaMalloc(&P->d_vt, vt_total);
+        if (e != cudaSuccess) {
+            if (P->d_acc) cudaFree(P->d_acc);
+            delete P;
+            return set_error(PYRONN_OOM, "transposed volumes: %s", cudaGetErrorString(e));
+        }
+    }
     e = cudaMalloc(&P->d_counter, 4 * sizeof(int));
     if (e != cudaSuccess) {
         if (P->d_acc) cudaFree(P->d_acc);
+        if (P->d_vt) cudaFree(P->d_vt);
         delete P;
         return set_error(PYRONN_OOM, "work counters: %s", cudaGetErrorString(e));
     }
@@ -155,6 +175,7 @@ int pyronn_plan_destroy(pyronn_plan_t P) {
     if (!P) return PYRONN_OK;
     if (P->d_counter) cudaFree(P->d_counter);
     if (P->d_acc) cudaFree(P->d_acc);
+    if (P->d_vt) cudaFree(P->d_vt);
     delete P;
     return PYRONN_OK;
 }
@@ -214,6 +235,7 @@ int pyronn_plan_fp(pyronn_plan_t P, const void *const *vols, void *const *sinos,
         V.cfg = P->cfg[i];
         V.in = vols[i];
         V.out = sinos[i];
+        V.vt = V.cfg.xt ? (void *)(P->d_vt + P->vt_off[i]) : nullptr;
         V.ntx = (g->nu + 15) / 16;
         V.nty = (g->nv + 15) / 16;
         V.ntz = 1;

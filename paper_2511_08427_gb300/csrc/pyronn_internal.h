@@ -102,6 +102,7 @@ struct FpTmaBox {
     int buf_elems;             // elements per buffer (max over axes)
     int nbuf;                  // 1 or 2 shared-memory buffers
     int minb;                  // CTAs per SM the single-volume kernel is compiled for (2 or 4)
+    int xt;                    // x-march boxes come from a y-fastest copy of the volume (y innermost)
 };
 
 // Slab-ordered adjoint configuration (chosen per geometry).
@@ -111,6 +112,7 @@ struct AdjSlabCfg {
     int valid;                 // 0: use the brick adjoint
     int allow_fixed;           // int32 fixed-point boxes where the per-slab bound allows
     int cell_fixed;            // fixed-point boxes: 1 cell-accumulated reductions, 0 one per sample
+    int xpad;                  // x-march boxes get an odd row pitch (one word more than the x extent)
 };
 
 // Batched (persistent) launches: per-volume descriptions of one plan, in processing order.
@@ -120,6 +122,7 @@ struct PlanVolume {
     FpTmaBox cfg;              // forward-projector boxes of this geometry and element type
     const void *in;            // input buffer (volume for FP, sinogram for adjoint / BP)
     void *out;                 // output buffer
+    void *vt;                  // FP with cfg.xt: buffer for the y-fastest copy of the volume
     int ntx, nty;              // work tiles: detector tiles (FP) or volume bricks in x, y (adjoint, BP)
     int ntz;                   // bricks in z (adjoint, BP)
     int per_item;              // views per item group: FP items are (view, tile)
@@ -140,6 +143,7 @@ struct Tuning {
     int fp_nbuf = 0;           // its number of buffers
     int fp_minb = 0;           // its CTAs per SM (2 or 4; 0 automatic)
     int adj_accum = 0;         // slab adjoint boxes: 0 automatic, 1 FP32 only, 2 fixed point with cells
+    int fp_transpose = 0;      // TMA forward projector, x-march tiles: 0 y-fastest copy where usable, 1 never
 };
 
 }  // namespace pyronn
@@ -178,6 +182,8 @@ struct pyronn_geom {
     int tex_batch = 0;             // volumes the array holds
     void *d_upd_sino = nullptr;    // work buffers of pyronn_adjoint_update on the unfused kernels
     void *d_upd_vol = nullptr;
+    void *d_vol_t = nullptr;           // y-fastest copy of the volume for the TMA forward projector
+    size_t vol_t_bytes = 0;
     size_t upd_sino_bytes = 0, upd_vol_bytes = 0;
     void *d_stage_in = nullptr;    // device buffers of the host-buffer entry points
     void *d_stage_out = nullptr;
@@ -207,8 +213,10 @@ int finalize_geometry(pyronn_geom *g);          // build FP32 tables from views
 int ensure_device(pyronn_geom *g);               // upload tables to the current device
 OpParams make_params(const pyronn_geom *g, int batch);
 FpSlabCfg choose_fp_slab_cfg(const pyronn_geom *g);
-FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf, int minb);
-int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *sino, int dtype, void *stream);
+FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf, int minb, int xt);
+// vol_t: device buffer of batch x volume elements for the y-fastest copy (used when cfg.xt)
+int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *vol_t, void *sino, int dtype,
+                  void *stream);
 int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int launch_adjoint_brick_batched(const PlanLaunch &L, int dtype, int grid, void *stream);
 int launch_residual(const void *a, const void *b, void *out, long long n, int dtype, void *stream);

@@ -23,7 +23,7 @@ from ._lib import BF16, BP_INV_W2, BP_PLAIN, F16, F32, DetDesc, VolDesc, check, 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 # tuning parameters of Geometry.set_tuning (pyronn_tuning_param)
-TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM, TUNE_FP_CTAS_PER_SM = 0, 1, 2, 3
+TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM, TUNE_FP_CTAS_PER_SM, TUNE_FP_TRANSPOSE = 0, 1, 2, 3, 4
 
 
 def _dp(a: np.ndarray):
@@ -167,12 +167,12 @@ class Geometry:
         return list(out)
 
     def fp_config(self, dtype=torch.float32) -> dict:
-        out = (ctypes.c_int * 16)()
+        out = (ctypes.c_int * 20)()
         check(lib().pyronn_geom_fp_config(self._h, _DTYPES[dtype], out))
         o = list(out)
         return {"kernel": o[0], "depth": o[1], "guard": o[2], "slab0": o[3],
                 "box": [o[4:7], o[7:10], o[10:13]], "buf_elems": o[13], "smem_bytes": o[14],
-                "thread_box_capacity": o[15]}
+                "thread_box_capacity": o[15], "y_fastest_x_march": bool(o[16])}
 
     def adjoint_config(self) -> dict:
         out = (ctypes.c_int * 4)()

@@ -132,20 +132,28 @@ def test_step_changes_sample_count(L):
 
 @pytest.mark.parametrize("dtype_size,dtype", [(4, "float32"), (2, "bfloat16")])
 def test_fp_config_invariants(L, dtype_size, dtype):
-    """TMA boxes: at most 256 per dimension, x extent a multiple of 16 bytes, first slab plane minus
-    the guard aligned (so x-march boxes start aligned), double buffer within 200 KB."""
+    """TMA boxes: at most 256 per dimension, innermost extent a multiple of 16 bytes (x, or y for
+    x-march boxes staged from the y-fastest copy), first slab plane minus the guard aligned (so
+    x-march boxes of the x-fastest volume start aligned), double buffer within 200 KB."""
     import torch
-    from paper_2511_08427_gb300.operators import Geometry
+    from paper_2511_08427_gb300.operators import TUNE_FP_TRANSPOSE, Geometry
     td = getattr(torch, dtype)
     g = Geometry.cone_circular((64, 96, 128), (0.5, 0.5, 0.5), (100, 130), (0.6, 0.6), 40, 2 * math.pi, 750.0, 1200.0)
-    c = g.fp_config(td)
-    assert c["kernel"] == 3
-    align = 16 // dtype_size
-    for box in c["box"]:
-        assert all(1 <= e <= 256 for e in box)
-        assert (box[0] * dtype_size) % 16 == 0
-    assert (c["slab0"] - c["guard"]) % align == 0
-    assert c["smem_bytes"] <= 200 * 1024 + 128
+    for transpose in (0, 1):
+        g.set_tuning(TUNE_FP_TRANSPOSE, transpose)
+        c = g.fp_config(td)
+        assert c["kernel"] == 3
+        assert c["y_fastest_x_march"] == (transpose == 0)     # ny * dtype_size is a multiple of 16
+        align = 16 // dtype_size
+        for m, box in enumerate(c["box"]):
+            assert all(1 <= e <= 256 for e in box)
+            inner = 1 if (m == 0 and c["y_fastest_x_march"]) else 0
+            assert (box[inner] * dtype_size) % 16 == 0
+        assert (c["slab0"] - c["guard"]) % align == 0
+        assert c["smem_bytes"] <= 200 * 1024 + 128
+    # a y extent that is not a multiple of 16 bytes keeps x-march boxes on the volume itself
+    g3 = Geometry.cone_circular((64, 90, 128), (0.5, 0.5, 0.5), (100, 130), (0.6, 0.6), 8, 2 * math.pi, 750.0, 1200.0)
+    assert g3.fp_config(td)["kernel"] == 3 and not g3.fp_config(td)["y_fastest_x_march"]
     # rows that are not a multiple of 16 bytes cannot use tensor copies
     g2 = Geometry.cone_circular((20, 20, 30), (0.5, 0.5, 0.5), (30, 30), (0.6, 0.6), 8, 2 * math.pi, 75.0, 120.0)
     assert g2.fp_config(td)["kernel"] == 2

@@ -73,6 +73,39 @@ def test_fp_matches_oracle(ops, case, variant):
     assert g.read_flags()[:4] == [0, 0, 0, 0]
 
 
+# y and x extents of 16-byte multiples in FP32 and BF16, so that x-march boxes of the TMA-staged
+# projector can come from the y-fastest copy of the volume; ragged detector, offsets
+YFAST = Case("cone_y_fastest", dict(kind="cone", vol_shape=(22, 24, 32), vol_spacing=(0.5, 0.45, 0.5),
+                                    det_shape=(23, 37), det_spacing=(0.6, 0.6), views=14, range=2 * math.pi,
+                                    sid=70.0, sdd=115.0, det_offset=(0.3, -0.6), vol_offset=(0.4, -0.2, 0.3)), 3)
+
+
+@pytest.mark.parametrize("transpose", [0, 1])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_fp_x_march_boxes_from_y_fastest_copy(ops, dtype, transpose):
+    """TMA-staged projector with the x-march boxes staged from the y-fastest copy of the volume
+    (transpose 0) and from the volume itself (1): both match the oracle on a batch of two volumes (the
+    copy covers every volume of the batch), and the two agree to rounding."""
+    g = YFAST.library_geometry()
+    g.set_variant(0, 3)
+    g.set_tuning(ops.TUNE_FP_TRANSPOSE, transpose)
+    cfg = g.fp_config(dtype)
+    assert cfg["kernel"] == 3 and cfg["y_fastest_x_march"] == (transpose == 0)
+    og = YFAST.oracle_geometry()
+    xs = np.stack([YFAST.phantom(seed=s) for s in (1, 2)])
+    xd = to_dev(xs, dtype)
+    xr = host(xd)
+    g.read_flags(reset=True)
+    p = host(ops.forward_project(xd, g))
+    assert g.read_flags()[:4] == [0, 0, 0, 0]
+    for i in range(2):
+        assert rel_l2(p[i], oracle.fp(og, xr[i])) <= TOL[dtype]
+    g.set_tuning(ops.TUNE_FP_TRANSPOSE, 1 - transpose)
+    q = host(ops.forward_project(xd, g))
+    # FP32 storage: the two differ by the order of the lerps only; BF16: also by output roundings
+    assert rel_l2(q, p) <= (1e-6 if dtype == torch.float32 else TOL[dtype])
+
+
 @pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("case", SMALL, ids=lambda c: c.name)
 def test_adjoint_matches_oracle(ops, case, variant):
