@@ -274,7 +274,9 @@ PYRONN_API int pyronn_plan_bp(pyronn_plan_t plan, const void *const *sinos, void
 
 /* Host-buffer variants: copy the input from host memory (pinned for best speed) into device
  * buffers owned by the geometry (allocated on first use), run the operator on `stream`, copy
- * the result back and synchronise the stream. */
+ * the result back and synchronise the stream. With the TMA-staged projector the forward
+ * projection runs the views in up to 8 chunks and downloads each chunk's sinogram rows on a
+ * geometry-owned stream while the next chunk runs (the volume's upload precedes every view). */
 PYRONN_API int pyronn_fp_host(pyronn_geom_t g, const void *vol_host, void *sino_host, int dtype, int batch, void *stream);
 PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void *vol_host, int dtype, int batch,
                         void *stream);

@@ -547,7 +547,7 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
     if (!g) return PYRONN_OK;
     // device buffers are freed on the device they were allocated on
     if (g->d_fp || g->d_scratch || g->d_stage_in || g->d_stage_out || g->d_upd_sino || g->d_upd_vol || g->d_fbp ||
-        g->d_vol_t || g->tex_arr) {
+        g->d_vol_t || g->copy_stream || g->tex_arr) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (g->device >= 0 && g->device != cur) cudaSetDevice(g->device);
@@ -562,6 +562,9 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
         cudaFree(g->d_upd_vol);
         cudaFree(g->d_fbp);
         cudaFree(g->d_vol_t);
+        for (void *ev : g->pipe_ev)
+            if (ev) cudaEventDestroy((cudaEvent_t)ev);
+        if (g->copy_stream) cudaStreamDestroy((cudaStream_t)g->copy_stream);
         if (g->tex_obj) cudaDestroyTextureObject((cudaTextureObject_t)g->tex_obj);
         if (g->tex_arr) cudaFreeArray((cudaArray_t)g->tex_arr);
         cudaFree(g->d_tex_org);

@@ -624,7 +624,7 @@ static int encode_maps(const OpParams &p, const FpTmaBox &cfg, const void *vol, 
 
 template <typename T>
 static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *vol_t, void *sino,
-                        cudaStream_t st) {
+                        cudaStream_t st, int make_copy) {
     if (cfg.xt && !vol_t) return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)cfg.nbuf * sizeof(T) * (size_t)cfg.buf_elems + 128;
     auto kern = cfg.minb == 4 ? fp_tma_kernel<T, 4> : fp_tma_kernel<T, 2>;
@@ -638,7 +638,7 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
         const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
         const T *vptr = (const T *)vol + b0 * p.vol_elems;
         T *tptr = cfg.xt ? (T *)vol_t + b0 * p.vol_elems : nullptr;
-        if (cfg.xt) {
+        if (cfg.xt && make_copy) {
             const long long nsl = (long long)nz * nb;
             dim3 tg(ceil_div(nx, 32), ceil_div(ny, 32), (unsigned)std::min<long long>(nsl, 65535));
             transpose_xy_kernel<T><<<tg, dim3(32, 8), 0, st>>>(vptr, tptr, nx, ny, nsl);
@@ -712,12 +712,12 @@ int fp_tma_batched_occupancy(int dtype, size_t smem, int *blocks_per_sm) {
 }
 
 int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *vol_t, void *sino, int dtype,
-                  void *stream) {
+                  void *stream, int make_copy) {
     cudaStream_t st = (cudaStream_t)stream;
     switch (dtype) {
-        case PYRONN_F32: return launch_tma_t<float>(p, cfg, vol, vol_t, sino, st);
-        case PYRONN_BF16: return launch_tma_t<__nv_bfloat16>(p, cfg, vol, vol_t, sino, st);
-        case PYRONN_F16: return launch_tma_t<__half>(p, cfg, vol, vol_t, sino, st);
+        case PYRONN_F32: return launch_tma_t<float>(p, cfg, vol, vol_t, sino, st, make_copy);
+        case PYRONN_BF16: return launch_tma_t<__nv_bfloat16>(p, cfg, vol, vol_t, sino, st, make_copy);
+        case PYRONN_F16: return launch_tma_t<__half>(p, cfg, vol, vol_t, sino, st, make_copy);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -410,6 +410,75 @@ int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype,
     return cuda_rc(launch_bp_transpose(p, vol, sino, acc, dtype, stream), "back-projection transpose launch");
 }
 
+// The stream and events of the overlapped downloads (created once per geometry, on its device).
+static int ensure_pipe(pyronn_geom_t g) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->copy_stream) return PYRONN_OK;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i < 9; ++i) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        g->pipe_ev[i] = ev;
+    }
+    if (e != cudaSuccess) {
+        for (void *&ev : g->pipe_ev)
+            if (ev) cudaEventDestroy((cudaEvent_t)ev), ev = nullptr;
+        if (s) cudaStreamDestroy(s);
+        return cuda_rc((int)e, "copy stream");
+    }
+    g->copy_stream = s;
+    return PYRONN_OK;
+}
+
+// Forward projection of host buffers with the download of the sinogram overlapped: the views are
+// projected in up to 8 chunks on `stream` (the volume's y-fastest copy is made once, by the first), and
+// each chunk's sinogram rows go back to the host on the geometry's copy stream as soon as the chunk is
+// done. Every view needs the whole volume, so its upload comes first. Only for the TMA projector.
+static int fp_host_overlapped(pyronn_geom_t g, const FpTmaBox &tb, const void *in_host, void *out_host, int dtype,
+                              int batch, cudaStream_t st) {
+    int rc;
+    if ((rc = ensure_pipe(g))) return rc;
+    const size_t es = dtype_size(dtype);
+    const size_t vol_bytes = es * (size_t)g->nx * g->ny * g->nz * batch;
+    const size_t view_bytes = es * (size_t)g->nu * g->nv;
+    const size_t sino_item = view_bytes * (size_t)g->n_views;   // one volume's sinogram
+    if (tb.xt && (rc = ensure_buffer(g, &g->d_vol_t, &g->vol_t_bytes, vol_bytes, "transposed volume"))) return rc;
+    cudaStream_t cs = (cudaStream_t)g->copy_stream;
+    cudaError_t e = cudaMemcpyAsync(g->d_stage_in, in_host, vol_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_rc((int)e, "host-to-device copy");
+    const OpParams p = make_params(g, batch);
+    const int nchunk = std::min(8, g->n_views);
+    for (int k = 0; k < nchunk; ++k) {
+        const int v0 = (int)((long long)g->n_views * k / nchunk), v1 = (int)((long long)g->n_views * (k + 1) / nchunk);
+        // views v0 .. v1 - 1: per-view tables and the sinogram start move by v0; the per-volume sinogram
+        // stride (sino_elems) stays that of all views
+        OpParams pc = p;
+        pc.n_views = v1 - v0;
+        pc.fp += v0;
+        pc.bp += v0;
+        pc.views64 += (size_t)v0 * VIEW64_STRIDE;
+        unsigned char *dev_k = (unsigned char *)g->d_stage_out + (size_t)v0 * view_bytes;
+        e = (cudaError_t)launch_fp_tma(pc, tb, g->d_stage_in, g->d_vol_t, dev_k, dtype, st, k == 0);
+        if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)g->pipe_ev[k], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, (cudaEvent_t)g->pipe_ev[k], 0);
+        for (int b = 0; e == cudaSuccess && b < batch; ++b)
+            e = cudaMemcpyAsync((unsigned char *)out_host + b * sino_item + (size_t)v0 * view_bytes,
+                                dev_k + b * sino_item, (size_t)(v1 - v0) * view_bytes, cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(cs);
+            return cuda_rc((int)e, "forward projection with overlapped download");
+        }
+    }
+    e = cudaEventRecord((cudaEvent_t)g->pipe_ev[8], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, (cudaEvent_t)g->pipe_ev[8], 0);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(cs);
+        return cuda_rc((int)e, "copy stream join");
+    }
+    return cuda_rc((int)cudaStreamSynchronize(st), "stream synchronise");
+}
+
 static int host_op(pyronn_geom_t g, const void *in_host, void *out_host, int dtype, int batch, void *stream, int fp) {
     clear_error();
     int rc = common_checks(g, dtype, batch);
@@ -422,6 +491,10 @@ static int host_op(pyronn_geom_t g, const void *in_host, void *out_host, int dty
     size_t in_bytes = fp ? vol_bytes : sino_bytes, out_bytes = fp ? sino_bytes : vol_bytes;
     if ((rc = ensure_stage(g, in_bytes, out_bytes))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    if (fp && (g->fp_variant == 0 || g->fp_variant == 3)) {
+        const FpTmaBox &tb = tma_cfg(g, dtype);
+        if (tb.depth > 0) return fp_host_overlapped(g, tb, in_host, out_host, dtype, batch, st);
+    }
     cudaError_t e = cudaMemcpyAsync(g->d_stage_in, in_host, in_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_rc((int)e, "host-to-device copy");
     rc = fp ? pyronn_fp(g, g->d_stage_in, g->d_stage_out, dtype, batch, stream)

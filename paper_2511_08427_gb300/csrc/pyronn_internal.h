@@ -184,6 +184,8 @@ struct pyronn_geom {
     void *d_upd_vol = nullptr;
     void *d_vol_t = nullptr;           // y-fastest copy of the volume for the TMA forward projector
     size_t vol_t_bytes = 0;
+    void *copy_stream = nullptr;       // host-buffer entry points: stream of the overlapped downloads
+    void *pipe_ev[9] = {};             // and the events that order it (one per view chunk, one final)
     size_t upd_sino_bytes = 0, upd_vol_bytes = 0;
     void *d_stage_in = nullptr;    // device buffers of the host-buffer entry points
     void *d_stage_out = nullptr;
@@ -214,9 +216,10 @@ int ensure_device(pyronn_geom *g);               // upload tables to the current
 OpParams make_params(const pyronn_geom *g, int batch);
 FpSlabCfg choose_fp_slab_cfg(const pyronn_geom *g);
 FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf, int minb, int xt);
-// vol_t: device buffer of batch x volume elements for the y-fastest copy (used when cfg.xt)
+// vol_t: device buffer of batch x volume elements for the y-fastest copy (used when cfg.xt); make_copy 0:
+// vol_t already holds the copy of vol (an earlier launch on the same stream made it)
 int launch_fp_tma(const OpParams &p, const FpTmaBox &cfg, const void *vol, void *vol_t, void *sino, int dtype,
-                  void *stream);
+                  void *stream, int make_copy = 1);
 int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int launch_adjoint_brick_batched(const PlanLaunch &L, int dtype, int grid, void *stream);
 int launch_residual(const void *a, const void *b, void *out, long long n, int dtype, void *stream);
