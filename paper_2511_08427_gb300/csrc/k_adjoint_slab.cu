@@ -53,7 +53,6 @@
 namespace pyronn {
 
 constexpr int AS_TU = 32, AS_TV = 32, AS_NT = 256, AS_RPT = 4;
-constexpr int AS_MAX_SLABS = 80;
 
 struct AsTile {                 // per tile (FP64-derived)
     float D[3], Cu[3], Cv[3];   // corner-ray direction and its per-pixel steps
@@ -72,10 +71,11 @@ struct AsSlab {                 // per (tile, slab), relative to the box centre 
     float scale, inv_scale;     // fixed-point scale 2^e and 2^-e; scale == 0: FP32 box
 };
 
+// per-tile state in static shared memory; the slab table (one AsSlab per slab of the tile, at most
+// cfg.max_slabs) lives in dynamic shared memory after the box
 struct AsShared {
     float corner[5][6];
     AsTile tile;
-    AsSlab slab[AS_MAX_SLABS];
     int srange[2];
     unsigned ymax;              // max |y| dt over the tile (FP32 bits)
     int nfixed;                 // slabs accumulated in fixed point
@@ -314,7 +314,8 @@ __device__ __forceinline__ void as_zero_box(float *box, int box_cap) {
 template <typename T>
 __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg, const T *__restrict__ sino,
                                         const T *__restrict__ sino_b, float y_scale, float *__restrict__ vol,
-                                        int view, int b, int tile_x, int tile_y, float *box, AsShared &sh) {
+                                        int view, int b, int tile_x, int tile_y, float *box, AsSlab *slabs,
+                                        AsShared &sh) {
     const int depth = cfg.depth, guard = cfg.guard, box_cap = cfg.box_cap;
     const int allow_fixed = cfg.allow_fixed, cell_fixed = cfg.cell_fixed;
     const int tu0 = tile_x * AS_TU, tv0 = tile_y * AS_TV;
@@ -430,12 +431,12 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
     // the box is all zero on entry; each flush zeroes what it added, so it is zero again for the next slab
     __syncthreads();
     const int s_first = sh.srange[0];
-    const int nsl = sh.srange[1] >= s_first ? min(sh.srange[1] - s_first + 1, AS_MAX_SLABS) : 0;
+    const int nsl = sh.srange[1] >= s_first ? min(sh.srange[1] - s_first + 1, cfg.max_slabs) : 0;
     if (nsl <= 0) return;
 
     // slab boxes (FP32 from the corner rays, as in the forward projector) and FP64 anchors, one lane per slab
     for (int i = tid; i < nsl; i += AS_NT) {
-        AsSlab &S = sh.slab[i];
+        AsSlab &S = slabs[i];
         const int s = s_first + i;
         const int b_lo = base0 + s * D;
         const int b_hi = min(b_lo + D, Nm);
@@ -506,7 +507,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
     const bool vec4 = (p.vol.nx & 3) == 0;
 
     for (int i = 0; i < nsl; ++i) {
-        const AsSlab &S = sh.slab[i];
+        const AsSlab &S = slabs[i];
         const int s = s_first + i;
         if (S.ext[0] == 0) {
             // the tile's footprint in this slab does not fit the box: never expected (the host bound
@@ -770,9 +771,10 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, AdjS
                                                                 float *__restrict__ vol) {
     extern __shared__ __align__(16) float box[];
     __shared__ AsShared sh;
+    AsSlab *slabs = reinterpret_cast<AsSlab *>(box + ((cfg.box_cap + 3) & ~3));
     as_zero_box(box, cfg.box_cap);
     as_tile<T>(p, cfg, sino, sino_b, y_scale, vol, blockIdx.z % p.n_views, blockIdx.z / p.n_views, blockIdx.x,
-               blockIdx.y, box, sh);
+               blockIdx.y, box, slabs, sh);
 }
 
 // Persistent launch over the (view, tile) items of several volumes (each with its own geometry and
@@ -783,8 +785,11 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_batched_kernel(const __
     extern __shared__ __align__(16) float box[];
     __shared__ AsShared sh;
     __shared__ long long s_item;
+    // one table position for every volume (after the largest box), so that no volume's table lands in
+    // another volume's (zeroed) box
     int cap = 0;
     for (int i = 0; i < L.n; ++i) cap = max(cap, L.v[i].acfg.box_cap);
+    AsSlab *slabs = reinterpret_cast<AsSlab *>(box + ((cap + 3) & ~3));
     as_zero_box(box, cap);
     const long long total = L.item_end[L.n - 1];
     for (;;) {
@@ -800,7 +805,7 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_batched_kernel(const __
         const int tiles = V.ntx * V.nty;
         const int view = (int)(local / tiles), t = (int)(local % tiles);
         as_tile<T>(V.p, V.acfg, (const T *)V.in, (const T *)nullptr, 1.0f, V.acc, view, 0, t % V.ntx, t / V.ntx,
-                   box, sh);
+                   box, slabs, sh);
     }
 }
 
@@ -884,36 +889,39 @@ static long long as_bound(const pyronn_geom *g, int depth, int guard, int xpad) 
     return best.load();
 }
 
-// Deepest slab (8, 6 or 4 planes, and at most AS_MAX_SLABS slabs per tile) whose box lets two CTAs
-// share an SM (224 KB of shared memory, 1 KB reserved per CTA, the static tile state), first
-// with the odd row pitch of x-march boxes, then without it; otherwise the shallowest that fits in
-// 160 KB (16-byte pitch).
+size_t adjoint_slab_smem_bytes(int box_cap, int max_slabs) {
+    return sizeof(float) * (size_t)((box_cap + 3) & ~3) + sizeof(AsSlab) * (size_t)max_slabs;
+}
+
+// Deepest slab (8, 6, 5 or 4 planes) whose box and slab table let two CTAs share an SM (224 KB of
+// shared memory, 1 KB reserved per CTA, the static tile state), first with the odd row pitch of x-march
+// boxes, then without it; otherwise the shallowest whose box fits in 160 KB (16-byte pitch).
 AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     AdjSlabCfg c{};
     if (g->ndim != 3) return c;
     const int nmax = std::max(g->nx, std::max(g->ny, g->nz));
-    const int dmin = (nmax + 2 + AS_MAX_SLABS - 1) / AS_MAX_SLABS;
     const double smin = std::min(g->sx, std::min(g->sy, g->sz));
     c.guard = 1 + (int)std::floor(g->dt / smin);
     // two CTAs per SM: 224 KB of the SM's shared memory, 1 KB reserved per CTA, the static tile
     // state (the occupancy calculator on GB300 admits two CTAs of 114264 bytes each, not of 115152)
-    const long long soft = ((224 * 1024) / 2 - 1024 - (long long)sizeof(AsShared) - 64) / 4;
+    const size_t soft = (224 * 1024) / 2 - 1024 - sizeof(AsShared) - 64;
     const long long hard = (160 * 1024) / 4;
     long long need = 0;
     bool fit = false;
     for (int xpad = 1; xpad >= 0 && !fit; --xpad)
-        for (int d : {8, 6, 4}) {
-            const int depth = std::max(d, dmin);
+        for (int depth : {8, 6, 5, 4}) {
             need = as_bound(g, depth, c.guard, xpad);
             c.depth = depth;
             c.xpad = xpad;
-            if (need <= soft) {
+            // slabs of a tile: planes -1 .. N, at most (N + 2 + depth - 1) / depth along any axis
+            c.max_slabs = (nmax + 2 + depth - 1) / depth;
+            if (need > 0 && adjoint_slab_smem_bytes((int)need, c.max_slabs) <= soft) {
                 fit = true;
                 break;
             }
         }
     c.box_cap = (int)std::min(need, hard);
-    c.valid = need > 0 && need <= hard;
+    c.valid = need > 0 && need <= hard && adjoint_slab_smem_bytes(c.box_cap, c.max_slabs) <= 200 * 1024;
     c.allow_fixed = g->tuning.adj_accum != 1;
     c.cell_fixed = g->tuning.adj_accum == 2;
     return c;
@@ -938,7 +946,7 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
     if (!accumulate) e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)n, st);
     else if ((void *)acc != vol) adjoint_widen_kernel<T><<<cblocks, 256, 0, st>>>((const T *)vol, acc, n);
     if (e != cudaSuccess) return (int)e;
-    const size_t smem = sizeof(float) * (size_t)c.box_cap;
+    const size_t smem = adjoint_slab_smem_bytes(c.box_cap, c.max_slabs);
     e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -121,14 +121,18 @@ int pyronn_plan_create(int n, const pyronn_geom_t *geoms, int dtype, pyronn_plan
     // slab-ordered adjoint for the whole plan if every geometry has a valid slab configuration
     P->adj_slab = true;
     size_t acc_total = 0;
+    int max_box = 0, max_slabs = 0;
     for (int i = 0; i < n; ++i) {
         const AdjSlabCfg &c = geom_adj_cfg(P->geoms[i]);
         P->acfg.push_back(c);
         P->acc_off.push_back(acc_total);
         acc_total += (size_t)P->geoms[i]->nx * P->geoms[i]->ny * P->geoms[i]->nz;
         if (!c.valid || (P->geoms[i]->adj_variant != 0 && P->geoms[i]->adj_variant != 3)) P->adj_slab = false;
-        P->adj_smem = std::max(P->adj_smem, sizeof(float) * (size_t)c.box_cap);
+        max_box = std::max(max_box, c.box_cap);
+        max_slabs = std::max(max_slabs, c.max_slabs);
     }
+    // the batched kernel puts every volume's slab table after the largest box
+    P->adj_smem = adjoint_slab_smem_bytes(max_box, max_slabs);
     if (P->adj_slab) {
         if ((e = (cudaError_t)adjoint_slab_batched_occupancy(P->adj_smem, &occ)) != cudaSuccess) {
             delete P;

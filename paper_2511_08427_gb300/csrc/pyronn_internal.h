@@ -109,6 +109,7 @@ struct FpTmaBox {
 struct AdjSlabCfg {
     int depth, guard;          // slab depth, guard planes
     int box_cap;               // shared-memory box capacity (floats)
+    int max_slabs;             // capacity of the per-tile slab table (dynamic shared memory, after the box)
     int valid;                 // 0: use the brick adjoint
     int allow_fixed;           // int32 fixed-point boxes where the per-slab bound allows
     int cell_fixed;            // fixed-point boxes: 1 cell-accumulated reductions, 0 one per sample
@@ -250,6 +251,9 @@ int launch_fp(const OpParams &p, const FpSlabCfg &cfg, const void *vol, void *si
 int launch_fp_direct(const OpParams &p, const void *vol, void *sino, int dtype, void *stream);
 int launch_adjoint(const OpParams &p, const void *sino, void *vol, float *acc32, int dtype, void *stream);
 int launch_adjoint_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
+// dynamic shared memory of a slab-adjoint CTA: the box (box_cap floats, rounded to 16 bytes), then the
+// slab table (max_slabs records)
+size_t adjoint_slab_smem_bytes(int box_cap, int max_slabs);
 AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g);
 int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino, const void *sino_b, float y_scale,
                         bool accumulate, void *vol, float *acc32, int dtype, void *stream);
