@@ -410,7 +410,18 @@ int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype,
     return cuda_rc(launch_bp_transpose(p, vol, sino, acc, dtype, stream), "back-projection transpose launch");
 }
 
-// The stream and events of the overlapped downloads (created once per geometry, on its device).
+// Views v0 .. v0 + n - 1 of p: per-view tables move by v0; the per-volume sinogram stride (sino_elems)
+// stays that of all views, so the caller offsets the sinogram pointer by v0 views.
+static OpParams view_range(const OpParams &p, int v0, int n) {
+    OpParams pc = p;
+    pc.n_views = n;
+    pc.fp += v0;
+    pc.bp += v0;
+    pc.views64 += (size_t)v0 * VIEW64_STRIDE;
+    return pc;
+}
+
+// The stream and events of the overlapped host copies (created once per geometry, on its device).
 static int ensure_pipe(pyronn_geom_t g) {
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->copy_stream) return PYRONN_OK;
@@ -451,13 +462,7 @@ static int fp_host_overlapped(pyronn_geom_t g, const FpTmaBox &tb, const void *i
     const int nchunk = std::min(8, g->n_views);
     for (int k = 0; k < nchunk; ++k) {
         const int v0 = (int)((long long)g->n_views * k / nchunk), v1 = (int)((long long)g->n_views * (k + 1) / nchunk);
-        // views v0 .. v1 - 1: per-view tables and the sinogram start move by v0; the per-volume sinogram
-        // stride (sino_elems) stays that of all views
-        OpParams pc = p;
-        pc.n_views = v1 - v0;
-        pc.fp += v0;
-        pc.bp += v0;
-        pc.views64 += (size_t)v0 * VIEW64_STRIDE;
+        const OpParams pc = view_range(p, v0, v1 - v0);
         unsigned char *dev_k = (unsigned char *)g->d_stage_out + (size_t)v0 * view_bytes;
         e = (cudaError_t)launch_fp_tma(pc, tb, g->d_stage_in, g->d_vol_t, dev_k, dtype, st, k == 0);
         if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)g->pipe_ev[k], st);

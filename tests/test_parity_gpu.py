@@ -432,6 +432,28 @@ def test_host_buffer_fp_overlapped_download(ops, transpose):
         assert torch.equal(ho, ref), pinned
 
 
+def test_host_buffer_adjoint(ops):
+    """pyronn_adjoint_host (FP32, slab adjoint), a batch of two from pageable and pinned host buffers:
+    matches the device-buffer adjoint and the oracle."""
+    import ctypes
+    from paper_2511_08427_gb300 import _lib
+    g = YFAST.library_geometry()
+    og = YFAST.oracle_geometry()
+    y = np.stack([inputs.gaussian(og.sino_shape, seed=s) for s in (61, 62)]).astype(np.float32)
+    ref = host(ops.adjoint(to_dev(y), g))
+    for pinned in (False, True):
+        hy = torch.from_numpy(y)
+        ho = torch.full(tuple(ref.shape), float("nan"))
+        if pinned:
+            hy, ho = hy.pin_memory(), ho.pin_memory()
+        _lib.check(_lib.lib().pyronn_adjoint_host(g.handle, ctypes.c_void_p(hy.data_ptr()),
+                                                  ctypes.c_void_p(ho.data_ptr()), 0, 2, None))
+        a = ho.numpy().astype(np.float64)
+        assert rel_l2(a, ref) <= 1e-6, pinned
+        for i in range(2):
+            assert rel_l2(a[i], oracle.adjoint(og, y[i].astype(np.float64))) <= 1e-5, (pinned, i)
+
+
 # ------------------------------------------------------------------------------------------------
 # benchmark configurations at full size
 # ------------------------------------------------------------------------------------------------
