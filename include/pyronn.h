@@ -313,13 +313,16 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * slabs of detector tiles that march along x from a y-fastest copy of the volume, made on the
  * call's stream into a geometry-owned buffer of the volume's size (allocated on first use), so that
  * the rays of a warp, which spread across y there, read consecutive shared-memory words; 1 stages
- * every slab from the volume itself. */
+ * every slab from the volume itself; PYRONN_TUNE_ADJ_PITCH: 0 (automatic) gives the slab-ordered
+ * adjoint's x-march boxes an odd row pitch (one word more than their x extent) wherever a slab depth
+ * still fits two CTAs per SM with it, 1 keeps rows of whole 16-byte groups. */
 typedef enum {
     PYRONN_TUNE_FP_DEPTH = 0,
     PYRONN_TUNE_FP_BUFFERS = 1,
     PYRONN_TUNE_ADJ_ACCUM = 2,
     PYRONN_TUNE_FP_CTAS_PER_SM = 3,
-    PYRONN_TUNE_FP_TRANSPOSE = 4
+    PYRONN_TUNE_FP_TRANSPOSE = 4,
+    PYRONN_TUNE_ADJ_PITCH = 5
 } pyronn_tuning_param;
 PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
 
@@ -345,9 +348,10 @@ PYRONN_API int pyronn_geom_read_flags(pyronn_geom_t g, int *out, int reset);
  * copy of the volume (their innermost TMA axis is then y), [17..19] zero. */
 PYRONN_API int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out);
 
-/* Matched-adjoint configuration (host computation, no GPU needed), 4 ints: [0] kernel (1 atomic
+/* Matched-adjoint configuration (host computation, no GPU needed), 8 ints: [0] kernel (1 atomic
  * scatter, 2 bricks, 3 slab-ordered), [1] slab depth, [2] guard planes, [3] shared-memory box
- * capacity in floats. */
+ * capacity in floats, [4] 1 if x-march boxes have an odd row pitch, [5] slab-table capacity,
+ * [6..7] zero. */
 PYRONN_API int pyronn_geom_adjoint_config(pyronn_geom_t g, int *out);
 
 /* Message describing the last error of the calling thread ("" if none). */

@@ -908,7 +908,7 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     const long long hard = (160 * 1024) / 4;
     long long need = 0;
     bool fit = false;
-    for (int xpad = 1; xpad >= 0 && !fit; --xpad)
+    for (int xpad = g->tuning.adj_pitch == 1 ? 0 : 1; xpad >= 0 && !fit; --xpad)
         for (int depth : {8, 6, 5, 4}) {
             need = as_bound(g, depth, c.guard, xpad);
             c.depth = depth;

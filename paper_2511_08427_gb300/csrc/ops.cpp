@@ -180,10 +180,13 @@ int pyronn_geom_adjoint_config(pyronn_geom_t g, int *out) {
     const AdjSlabCfg &ac = adj_cfg(g);
     int kernel = g->adj_variant == 1 ? 1 : 2;
     if ((g->adj_variant == 0 || g->adj_variant == 3) && ac.valid) kernel = 3;
+    for (int i = 0; i < 8; ++i) out[i] = 0;
     out[0] = kernel;
     out[1] = ac.depth;
     out[2] = ac.guard;
     out[3] = ac.box_cap;
+    out[4] = ac.xpad;
+    out[5] = ac.max_slabs;
     return PYRONN_OK;
 }
 
@@ -204,6 +207,11 @@ int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
             if (value != 0 && value != 2 && value != 4)
                 return set_error(PYRONN_INVALID_ARG, "CTAs per SM must be 0 (automatic), 2 or 4 (got %d)", value);
             g->tuning.fp_minb = value;
+            break;
+        case PYRONN_TUNE_ADJ_PITCH:
+            if (value < 0 || value > 1) return set_error(PYRONN_INVALID_ARG, "pitch mode %d out of [0, 1]", value);
+            g->tuning.adj_pitch = value;
+            g->adj_cfg_ready = 0;
             break;
         case PYRONN_TUNE_FP_TRANSPOSE:
             if (value < 0 || value > 1) return set_error(PYRONN_INVALID_ARG, "transpose mode %d out of [0, 1]", value);

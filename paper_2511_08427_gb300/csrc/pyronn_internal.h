@@ -145,6 +145,7 @@ struct Tuning {
     int fp_minb = 0;           // its CTAs per SM (2 or 4; 0 automatic)
     int adj_accum = 0;         // slab adjoint boxes: 0 automatic, 1 FP32 only, 2 fixed point with cells
     int fp_transpose = 0;      // TMA forward projector, x-march tiles: 0 y-fastest copy where usable, 1 never
+    int adj_pitch = 0;         // slab adjoint, x-march boxes: 0 odd row pitch where it fits, 1 16-byte pitch
 };
 
 }  // namespace pyronn

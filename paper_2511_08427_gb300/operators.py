@@ -23,7 +23,7 @@ from ._lib import BF16, BP_INV_W2, BP_PLAIN, F16, F32, DetDesc, VolDesc, check, 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 # tuning parameters of Geometry.set_tuning (pyronn_tuning_param)
-TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM, TUNE_FP_CTAS_PER_SM, TUNE_FP_TRANSPOSE = 0, 1, 2, 3, 4
+TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM, TUNE_FP_CTAS_PER_SM, TUNE_FP_TRANSPOSE, TUNE_ADJ_PITCH = 0, 1, 2, 3, 4, 5
 
 
 def _dp(a: np.ndarray):
@@ -175,9 +175,10 @@ class Geometry:
                 "thread_box_capacity": o[15], "y_fastest_x_march": bool(o[16])}
 
     def adjoint_config(self) -> dict:
-        out = (ctypes.c_int * 4)()
+        out = (ctypes.c_int * 8)()
         check(lib().pyronn_geom_adjoint_config(self._h, out))
-        return {"kernel": out[0], "depth": out[1], "guard": out[2], "box_floats": out[3]}
+        return {"kernel": out[0], "depth": out[1], "guard": out[2], "box_floats": out[3], "odd_pitch": bool(out[4]),
+                "max_slabs": out[5]}
 
     def set_tuning(self, param: int, value: int) -> None:
         check(lib().pyronn_geom_set_tuning(self._h, int(param), int(value)))

@@ -161,6 +161,25 @@ def test_fp_config_invariants(L, dtype_size, dtype):
     assert g2.fp_config(td)["kernel"] == 1
 
 
+def test_adjoint_config_invariants(L):
+    """Slab adjoint: the slab table holds every slab of the longest axis at the chosen depth; box and
+    table fit the two-CTAs-per-SM budget (112 KB each); the odd x-march pitch is on by default and the
+    16-byte pitch (PYRONN_TUNE_ADJ_PITCH = 1) needs no larger box."""
+    from paper_2511_08427_gb300.operators import TUNE_ADJ_PITCH, Geometry
+    g = Geometry.cone_circular((64, 96, 128), (0.5, 0.5, 0.5), (100, 130), (0.6, 0.6), 40, 2 * math.pi, 750.0, 1200.0)
+    c = g.adjoint_config()
+    assert c["kernel"] == 3 and c["odd_pitch"]
+    assert c["depth"] in (8, 6, 5, 4)
+    assert c["max_slabs"] == (128 + 2 + c["depth"] - 1) // c["depth"]
+    assert 4 * ((c["box_floats"] + 3) // 4 * 4) + 104 * c["max_slabs"] <= 112 * 1024
+    g.set_tuning(TUNE_ADJ_PITCH, 1)
+    c1 = g.adjoint_config()
+    assert c1["kernel"] == 3 and not c1["odd_pitch"]
+    assert c1["depth"] < c["depth"] or c1["box_floats"] <= c["box_floats"]
+    g.set_tuning(TUNE_ADJ_PITCH, 0)
+    assert g.adjoint_config() == c
+
+
 def test_argument_checks_precede_the_device(L):
     """Every entry point rejects bad arguments before touching the device (these run without a GPU):
     empty batches, volumes too large for 32-bit indexing, unknown filters, non-finite steps, jitter

@@ -182,6 +182,23 @@ def test_slab_adjoint_spiky_sinogram(ops):
     assert rel_l2(small, oracle.adjoint(og, base)) <= 5e-3
 
 
+@pytest.mark.parametrize("pitch", [0, 1])
+@pytest.mark.parametrize("case", SMALL3, ids=lambda c: c.name)
+def test_slab_adjoint_box_pitch(ops, case, pitch):
+    """x-march boxes with the odd row pitch (0, automatic) and with rows of whole 16-byte groups (1):
+    both match the oracle."""
+    g = case.library_geometry()
+    g.set_variant(1, 3)
+    g.set_tuning(ops.TUNE_ADJ_PITCH, pitch)
+    assert g.adjoint_config()["odd_pitch"] == (pitch == 0)
+    og = case.oracle_geometry()
+    y = inputs.gaussian(og.sino_shape, seed=26)
+    g.read_flags(reset=True)
+    a = host(ops.adjoint(to_dev(y), g))
+    assert rel_l2(a, oracle.adjoint(og, y)) <= 1e-5
+    assert g.read_flags()[:4] == [0, 0, 0, 0]
+
+
 def test_slab_adjoint_dense_rays_keep_fp32_boxes(ops):
     """Detector pixels much smaller than the voxels (many rays per voxel support): the bound on the
     box values exceeds the fixed-point budget and the boxes stay FP32; the operator is unchanged."""
