@@ -43,10 +43,13 @@ FP_SMEM_BYTES_PER_SAMPLE = 32   # eight FP32 interpolation operands
 ADJ_FLOP_PER_SAMPLE = 33    # 3 position FMA (6), 3 frac (3), 1 - a (2), z split (2), 12 weight products, 8 adds
 ADJ_RED_PER_SAMPLE = 8      # one scatter-add per trilinear corner
 BP_FLOP_PER_UPDATE = 18     # projection 3 FMA (6), reciprocal and 2 products (3), 3 bilinear lerps (6), weight, add
-# Shared-memory rates per clock per SM measured on GB300 (2070 MHz) with
-# python -m paper_2511_08427_gb300.peaks (every lane of 4 CTAs x 256 threads per SM, distinct banks):
+# On-chip rates per clock per SM measured on GB300 (2070 MHz) with
+# python -m paper_2511_08427_gb300.peaks (every lane of 4 CTAs x 256 threads per SM, distinct banks or
+# one cache line per warp request):
 SMEM_RED_PER_CLK_SM = 28.32        # int32 red.shared.add
 SMEM_LD_BYTES_PER_CLK_SM = 4 * 27.66   # 32-bit ld.shared
+L1_LDG_PER_CLK_SM = 17.2           # 32-bit global loads hitting L1 (read-only path), one line per warp request
+BP_LOADS_PER_UPDATE = 4            # bilinear detector operands
 
 
 def _env_int(name, default):
@@ -454,6 +457,12 @@ def run_gpu(args):
     rl_bp = alu_roofline("bp_brick_kernel", "paper_2511_08427_gb300/csrc/k_bp_brick.cu",
                          n_updates * BP_FLOP_PER_UPDATE, bp_s)
     rl_bp["flop_per_update"] = BP_FLOP_PER_UPDATE
+    ldg_rate = n_updates * BP_LOADS_PER_UPDATE / bp_s / 1e9
+    ldg_peak = n_sm * L1_LDG_PER_CLK_SM * sm_max * 1e6 / 1e9
+    rl_bp["l1_loads"] = {"achieved_gops": ldg_rate, "peak_gops": ldg_peak, "frac": ldg_rate / ldg_peak,
+                         "per_update": BP_LOADS_PER_UPDATE,
+                         "peak_source": f"{n_sm} SMs x {L1_LDG_PER_CLK_SM} L1-hit 32-bit ld.global/clk (measured) "
+                                        f"x {sm_max:.0f} MHz"}
     # kernels of one step: FP (plus the y-fastest copy it stages x-march slabs from), adjoint, BP
     fpc = g.fp_config()
     launches_per_step = 3 + (1 if fpc["kernel"] == 3 and fpc["y_fastest_x_march"] else 0)

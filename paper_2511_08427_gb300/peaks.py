@@ -3,8 +3,9 @@
     python -m paper_2511_08427_gb300.peaks
 
 Builds peaks.cu (beside this file) for sm_103a and prints one JSON line: int32 and FP32 shared-memory reductions,
-conflict-free 32-bit shared-memory loads and FP32 FMAs, each per clock per SM (clock = the device's
-reported maximum SM clock; a run at a lower clock reads proportionally lower).
+conflict-free 32-bit shared-memory loads, FP32 FMAs, and L1-resident 32-bit global loads (read-only path) and
+texture point fetches, each per clock per SM (clock = the device's reported maximum SM clock; a run at a
+lower clock reads proportionally lower).
 """
 from __future__ import annotations
 
