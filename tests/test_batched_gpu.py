@@ -96,6 +96,24 @@ def test_plan_bf16_storage(ops):
         assert rel_l2(host(adj[i]), oracle.adjoint(og, host(sinos[i]))) <= 4e-3, i
 
 
+def test_plan_mixes_y_fastest_and_plain_staging(ops):
+    """One persistent FP launch over volumes whose x-march slabs come from a y-fastest copy and volumes
+    staged from the volume itself (PYRONN_TUNE_FP_TRANSPOSE set per geometry before the plan is made):
+    every volume matches its per-geometry projection."""
+    lib_g, _, vols = small_batch(ops)
+    for i, g in enumerate(lib_g):
+        g.set_tuning(ops.TUNE_FP_TRANSPOSE, i % 2)
+    assert any(g.fp_config()["y_fastest_x_march"] for g in lib_g)
+    assert any(g.fp_config()["kernel"] == 3 and not g.fp_config()["y_fastest_x_march"] for g in lib_g)
+    plan = ops.Plan(lib_g)
+    xs = [torch.from_numpy(v).to(DEV) for v in vols]
+    sinos = [torch.full(g.sinogram_shape, float("nan"), device=DEV) for g in lib_g]
+    plan.forward_project(xs, sinos)
+    torch.cuda.synchronize()
+    for i, g in enumerate(lib_g):
+        assert rel_l2(host(sinos[i]), host(ops.forward_project(xs[i], g))) <= 1e-6, i
+
+
 def test_plan_under_cuda_graph(ops):
     lib_g, _, vols = small_batch(ops)
     plan = ops.Plan(lib_g)

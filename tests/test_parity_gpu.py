@@ -425,8 +425,9 @@ def test_host_buffer_entry_point(ops):
     assert rel_l2(out, oracle_fp(case, x)) <= 1e-5
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("transpose", [0, 1])
-def test_host_buffer_fp_overlapped_download(ops, transpose):
+def test_host_buffer_fp_overlapped_download(ops, transpose, dtype):
     """pyronn_fp_host on the TMA projector projects the views in chunks and downloads each chunk's rows
     on a second stream while the next chunk runs (14 views: chunks of one and two views). A batch of two,
     from pageable and from pinned host buffers, equals the device-buffer projection exactly (every ray's
@@ -437,15 +438,16 @@ def test_host_buffer_fp_overlapped_download(ops, transpose):
     g.set_variant(0, 3)
     g.set_tuning(ops.TUNE_FP_TRANSPOSE, transpose)
     assert g.fp_config()["kernel"] == 3
-    xs = np.stack([YFAST.phantom(seed=s) for s in (3, 4)]).astype(np.float32)
-    ref = ops.forward_project(to_dev(xs), g).cpu()
+    xs = torch.from_numpy(np.stack([YFAST.phantom(seed=s) for s in (3, 4)]).astype(np.float32)).to(dtype)
+    ref = ops.forward_project(xs.to(DEV), g).cpu()
+    code = {torch.float32: _lib.F32, torch.bfloat16: _lib.BF16}[dtype]
     for pinned in (False, True):
-        hx = torch.from_numpy(xs)
-        ho = torch.full(tuple(ref.shape), float("nan"))
+        hx = xs.clone()
+        ho = torch.full(tuple(ref.shape), float("nan"), dtype=dtype)
         if pinned:
             hx, ho = hx.pin_memory(), ho.pin_memory()
         _lib.check(_lib.lib().pyronn_fp_host(g.handle, ctypes.c_void_p(hx.data_ptr()), ctypes.c_void_p(ho.data_ptr()),
-                                             0, 2, None))
+                                             code, 2, None))
         assert torch.equal(ho, ref), pinned
 
 
