@@ -9,7 +9,9 @@
 // w = w0 + Pw . d. Every FP32 quantity is of the size of the brick's footprint, so the bilinear
 // weights carry ~1e-6-pixel errors instead of the ~1e-5 of absolute FP32 detector coordinates.
 // Along the column the three numerators advance by one addition each; when a view's u and w do
-// not depend on z (circular orbits) only v is recomputed.
+// not depend on z (circular orbits) only v is recomputed, and where every voxel of a warp's columns
+// reads all four taps on the detector (each lane tests its column's end voxels, the warp votes) the
+// warp reads them without bounds tests.
 #include "device_common.cuh"
 
 namespace pyronn {
@@ -131,13 +133,41 @@ __device__ __forceinline__ void bp_brick(const OpParams &p, const T *__restrict_
             float nb = fmaf(V.Qb[0], dx, fmaf(V.Qb[1], dy, V.Qb[2] * dz0));
             float w = fmaf(V.Pw[0], dx, fmaf(V.Pw[1], dy, fmaf(V.Pw[2], dz0, V.w0)));
             if (V.flat) {
-                if (!(w > 0.0f)) continue;
-                const float iw = __frcp_rn(w);
+                // Every lane of the warp is here (the view loop and the branches above are uniform): each
+                // tests its own column, u fixed and v monotone in z (v_z = fma(z, Qb_z, nb) scaled by 1/w),
+                // so the first and last voxel bound it; if all lanes' four taps lie on the detector, the
+                // warp reads them without bounds tests
+                const bool wpos = w > 0.0f;
+                const float iw = wpos ? __frcp_rn(w) : 0.0f;
+                const float qu = fmaf(na, iw, V.fu);
+                const float qv0 = fmaf(nb, iw, V.fv), qv1 = fmaf(fmaf((float)(BZ - 1), V.Qb[2], nb), iw, V.fv);
+                const float lu = -(float)V.U0, hu = (float)(nu - 1 - V.U0);
+                const float lv = -(float)V.V0, hv = (float)(nv - 1 - V.V0);
+                const bool ok = wpos && qu >= lu && qu < hu && qv0 >= lv && qv0 < hv && qv1 >= lv && qv1 < hv;
+                const float om = W2 ? iw * iw : 1.0f;
+                if (__all_sync(0xffffffffu, ok)) {
+                    const float tu = __fadd_rd(qu, 12582912.0f);
+                    const float au = qu - (tu - 12582912.0f);
+                    const T *qc = q + (__float_as_int(tu) - 0x4B400000 + V.U0);
+#pragma unroll
+                    for (int z = 0; z < BZ; ++z) {
+                        const float qv = fmaf(fmaf((float)z, V.Qb[2], nb), iw, V.fv);
+                        const float t = __fadd_rd(qv, 12582912.0f);
+                        const float av = qv - (t - 12582912.0f);
+                        const T *r = qc + (__float_as_int(t) - 0x4B400000 + V.V0) * nu;
+                        const float q00 = ldg_f32(r), q01 = ldg_f32(r + 1);
+                        const float q10 = ldg_f32(r + nu), q11 = ldg_f32(r + nu + 1);
+                        const float r0 = fmaf(au, q01 - q00, q00);
+                        const float r1 = fmaf(au, q11 - q10, q10);
+                        acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
+                    }
+                    continue;
+                }
+                if (!wpos) continue;
                 int iu;
                 float au;
-                magic_floor(fmaf(na, iw, V.fu), iu, au);
+                magic_floor(qu, iu, au);
                 iu += V.U0;
-                const float om = W2 ? iw * iw : 1.0f;
                 // the column iu and its bounds are shared by the brick's z voxels (32-bit detector
                 // indices: one view holds fewer than 2^31 pixels)
                 const bool u0 = (unsigned)iu < (unsigned)nu, u1 = (unsigned)(iu + 1) < (unsigned)nu;
@@ -145,7 +175,7 @@ __device__ __forceinline__ void bp_brick(const OpParams &p, const T *__restrict_
                 for (int z = 0; z < BZ; ++z) {
                     int iv;
                     float av;
-                    magic_floor(fmaf(nb, iw, V.fv), iv, av);
+                    magic_floor(fmaf(fmaf((float)z, V.Qb[2], nb), iw, V.fv), iv, av);
                     iv += V.V0;
                     const bool v0 = (unsigned)iv < (unsigned)nv, v1 = (unsigned)(iv + 1) < (unsigned)nv;
                     const T *r = q + (iv * nu + iu);
@@ -156,7 +186,6 @@ __device__ __forceinline__ void bp_brick(const OpParams &p, const T *__restrict_
                     const float r0 = fmaf(au, q01 - q00, q00);
                     const float r1 = fmaf(au, q11 - q10, q10);
                     acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
-                    nb += V.Qb[2];
                 }
             } else {
 #pragma unroll
