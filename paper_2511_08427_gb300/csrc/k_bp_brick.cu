@@ -216,8 +216,9 @@ __device__ __forceinline__ void bp_brick(const OpParams &p, const T *__restrict_
     }
 }
 
+// four CTAs per SM (64 registers): the loop is latency-bound on its L1 detector reads at three
 template <typename T, int BZ, bool W2>
-__global__ void __launch_bounds__(BPB_NT) bp_brick_kernel(OpParams p, const T *__restrict__ sino,
+__global__ void __launch_bounds__(BPB_NT, 4) bp_brick_kernel(OpParams p, const T *__restrict__ sino,
                                                           T *__restrict__ vol) {
     __shared__ BpView sv[BPB_CHUNK];
     const int nbz = (p.vol.nz + BZ - 1) / BZ;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(BPB_NT) bp_brick_kernel(OpParams p, const T *_
 
 // Persistent launch over the bricks of several volumes.
 template <typename T, bool W2>
-__global__ void __launch_bounds__(BPB_NT) bp_brick_batched_kernel(const __grid_constant__ PlanLaunch L) {
+__global__ void __launch_bounds__(BPB_NT, 4) bp_brick_batched_kernel(const __grid_constant__ PlanLaunch L) {
     __shared__ BpView sv[BPB_CHUNK];
     __shared__ int s_item;
     const long long total = L.item_end[L.n - 1];
