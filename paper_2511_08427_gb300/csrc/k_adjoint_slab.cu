@@ -169,6 +169,18 @@ __device__ float as_ray_bound(const float (*corner)[6], int m, int a1, int a2, c
                               int wv) {
     const float cap = (float)(wu * wv);
     if (wu < 2 || wv < 2) return cap;
+    // the count below treats the pixel-to-plane map as nearly affine over the tile; for tiles whose rays
+    // spread by more than ~11 degrees from the centre ray (extreme fan angles) it falls back to all rays
+    {
+        const float *cc = corner[4];
+        const float nc = sqrtf(cc[3] * cc[3] + cc[4] * cc[4] + cc[5] * cc[5]);
+        for (int c = 0; c < 4; ++c) {
+            const float *r = corner[c];
+            const float dot = r[3] * cc[3] + r[4] * cc[4] + r[5] * cc[5];
+            const float nr = sqrtf(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+            if (!(dot > 0.98f * nr * nc)) return cap;
+        }
+    }
     float s1 = 0.0f, s2 = 0.0f;
     for (int c = 0; c < 4; ++c) {
         const float idm = 1.0f / corner[c][3 + m];
@@ -641,66 +653,72 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                 }
                 continue;
             }
+            // FP32 boxes (and fixed-point boxes in cell mode): a ray's weights are summed in registers while
+            // it stays in one cell of the box and flushed with eight reductions when it moves on. A sample
+            // whose 2 x 2 x 2 block is not in the box (where the corner rays do not bound the tile's rays:
+            // extreme fan angles) flushes the pending cell and adds its corners inside the volume straight
+            // to global memory.
             float a0 = 0.f, a1v = 0.f, a2v = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f, a7 = 0.f;
-            int pix = 0, piy = 0, piz = 0, pkey = -1;
+            int pcell = -1;   // box offset of the pending cell, -1: none
             float jj = jf;
             for (int k = ka; k <= kb + 1; ++k, jj += 1.0f) {
-                int key = -2, ix = 0, iy = 0, iz = 0;
+                int cell = -1, ix = 0, iy = 0, iz = 0;
                 float ax = 0.f, ay = 0.f, az = 0.f;
+                bool off_box = false;
                 if (k <= kb) {
                     const float sj = fmaf(jj, dt, c_r);
                     as_floor_frac(fmaf(sj, qd0, qP0), ix, ax);
                     as_floor_frac(fmaf(sj, qd1, qP1), iy, ay);
                     as_floor_frac(fmaf(sj, qd2, qP2), iz, az);
-                    key = ((iz + 16) << 20) | ((iy + 16) << 10) | (ix + 16);
+                    if ((unsigned)ix < (unsigned)(Ex - 1) && (unsigned)iy < (unsigned)(Ey - 1) &&
+                        (unsigned)iz < (unsigned)(Ez - 1))
+                        cell = (iz * Ey + iy) * Px + ix;
+                    else
+                        off_box = true;
                 }
-                if (key != pkey) {
-                    if (pkey >= 0) {
-                        if ((unsigned)pix < (unsigned)(Ex - 1) && (unsigned)piy < (unsigned)(Ey - 1) &&
-                            (unsigned)piz < (unsigned)(Ez - 1)) {
-                            // the cell's 2 x 2 x 2 block lies in the box: eight reductions (corners outside the
-                            // volume land in the box margin and are dropped when the box is added)
-                            const unsigned a = box_base + 4u * (unsigned)((piz * Ey + piy) * Px + pix);
-                            if (fx) {
-                                as_red_shared_s32(a, __float2int_rn(a0));
-                                as_red_shared_s32(a + 4u, __float2int_rn(a1v));
-                                as_red_shared_s32(a + sy4, __float2int_rn(a2v));
-                                as_red_shared_s32(a + sy4 + 4u, __float2int_rn(a3));
-                                as_red_shared_s32(a + sz4, __float2int_rn(a4));
-                                as_red_shared_s32(a + sz4 + 4u, __float2int_rn(a5));
-                                as_red_shared_s32(a + sz4 + sy4, __float2int_rn(a6));
-                                as_red_shared_s32(a + sz4 + sy4 + 4u, __float2int_rn(a7));
-                            } else {
-                                as_red_shared(a, a0);
-                                as_red_shared(a + 4u, a1v);
-                                as_red_shared(a + sy4, a2v);
-                                as_red_shared(a + sy4 + 4u, a3);
-                                as_red_shared(a + sz4, a4);
-                                as_red_shared(a + sz4 + 4u, a5);
-                                as_red_shared(a + sz4 + sy4, a6);
-                                as_red_shared(a + sz4 + sy4 + 4u, a7);
-                            }
-                        } else {
-                            const float vals[8] = {a0, a1v, a2v, a3, a4, a5, a6, a7};
-                            as_out_of_box(p, vb, pix + lo0, piy + lo1, piz + lo2, vals, fx ? isc : 1.0f);
-                        }
+                if (cell != pcell && pcell >= 0) {
+                    // the cell's 2 x 2 x 2 block lies in the box: eight reductions (corners outside the volume
+                    // land in the box margin and are dropped when the box is added)
+                    const unsigned a = box_base + 4u * (unsigned)pcell;
+                    if (fx) {
+                        as_red_shared_s32(a, __float2int_rn(a0));
+                        as_red_shared_s32(a + 4u, __float2int_rn(a1v));
+                        as_red_shared_s32(a + sy4, __float2int_rn(a2v));
+                        as_red_shared_s32(a + sy4 + 4u, __float2int_rn(a3));
+                        as_red_shared_s32(a + sz4, __float2int_rn(a4));
+                        as_red_shared_s32(a + sz4 + 4u, __float2int_rn(a5));
+                        as_red_shared_s32(a + sz4 + sy4, __float2int_rn(a6));
+                        as_red_shared_s32(a + sz4 + sy4 + 4u, __float2int_rn(a7));
+                    } else {
+                        as_red_shared(a, a0);
+                        as_red_shared(a + 4u, a1v);
+                        as_red_shared(a + sy4, a2v);
+                        as_red_shared(a + sy4 + 4u, a3);
+                        as_red_shared(a + sz4, a4);
+                        as_red_shared(a + sz4 + 4u, a5);
+                        as_red_shared(a + sz4 + sy4, a6);
+                        as_red_shared(a + sz4 + sy4 + 4u, a7);
                     }
                     a0 = a1v = a2v = a3 = a4 = a5 = a6 = a7 = 0.f;
-                    pkey = key;
-                    pix = ix; piy = iy; piz = iz;
                 }
-                if (k <= kb) {
-                    const float wz1 = ys * az, wz0 = ys - wz1;
-                    const float w00 = wz0 * (1.f - ay), w01 = wz0 * ay, w10 = wz1 * (1.f - ay), w11 = wz1 * ay;
-                    a0 = fmaf(w00, 1.f - ax, a0);
-                    a1v = fmaf(w00, ax, a1v);
-                    a2v = fmaf(w01, 1.f - ax, a2v);
-                    a3 = fmaf(w01, ax, a3);
-                    a4 = fmaf(w10, 1.f - ax, a4);
-                    a5 = fmaf(w10, ax, a5);
-                    a6 = fmaf(w11, 1.f - ax, a6);
-                    a7 = fmaf(w11, ax, a7);
+                pcell = cell;
+                if (k > kb) break;
+                const float wz1 = ys * az, wz0 = ys - wz1;
+                const float w00 = wz0 * (1.f - ay), w01 = wz0 * ay, w10 = wz1 * (1.f - ay), w11 = wz1 * ay;
+                if (off_box) {
+                    const float vals[8] = {w00 * (1.f - ax), w00 * ax, w01 * (1.f - ax), w01 * ax,
+                                           w10 * (1.f - ax), w10 * ax, w11 * (1.f - ax), w11 * ax};
+                    as_out_of_box(p, vb, ix + lo0, iy + lo1, iz + lo2, vals, fx ? isc : 1.0f);
+                    continue;
                 }
+                a0 = fmaf(w00, 1.f - ax, a0);
+                a1v = fmaf(w00, ax, a1v);
+                a2v = fmaf(w01, 1.f - ax, a2v);
+                a3 = fmaf(w01, ax, a3);
+                a4 = fmaf(w10, 1.f - ax, a4);
+                a5 = fmaf(w10, ax, a5);
+                a6 = fmaf(w11, 1.f - ax, a6);
+                a7 = fmaf(w11, ax, a7);
             }
         }
         __syncthreads();

@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(TU *TV) fp_slab_kernel(OpParams p, FpSlabCfg c
         const int Ex = hi[0] - lo[0] + 1, Ey = hi[1] - lo[1] + 1, Ez = hi[2] - lo[2] + 1;
         // also acts as the barrier that ends the previous slab's reads of sbox
         if (!__syncthreads_or(ka <= kb)) continue;
-        if (Ex <= 0 || Ey <= 0 || Ez <= 0) continue;   // uniform: no sample can be inside
-        const bool staged = (long long)Ex * Ey * Ez <= cfg.smem_floats;
+        // an empty box (corner rays crossing the planes far outside the volume, as tiles of extreme fan
+        // angles can) does not mean the tile's other rays miss it: such slabs take the global path too
+        const bool staged = Ex > 0 && Ey > 0 && Ez > 0 && (long long)Ex * Ey * Ez <= cfg.smem_floats;
         if (staged) {
             // rows of the box (fixed y, z) are contiguous along x in memory and in shared memory
             const int rows = Ey * Ez;

@@ -274,7 +274,6 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 // loop's "x" and "y" below are the first and second axes
                 const int BF = yt ? BYb : BXb, BS = yt ? BXb : BYb;
                 const int sy = BF, sz = BF * BS;
-                const int limit = box_elems - (sz + sy + 1);
                 // floor(q) + 2^23 + 2^22 is the bit pattern of q + 1.5 2^23 rounded down, so the box offset
                 // sum floor(q_a) stride_a comes straight from the three bit patterns (unsigned wrap-around)
                 const unsigned boff = 0x4B400000u * (unsigned)(sz + sy + 1);
@@ -332,7 +331,12 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                         const float tx = __fadd_rd(qx, M), ty = __fadd_rd(qy, M), tz = __fadd_rd(qz, M);
                         const int base = (int)((unsigned)__float_as_int(tz) * (unsigned)sz +
                                                ((unsigned)__float_as_int(ty) * (unsigned)sy + ((unsigned)__float_as_int(tx) - boff)));
-                        if ((unsigned)base > (unsigned)limit) {
+                        // per-axis cell index in the box; a position outside (-2^22, 2^22), or NaN, gives an
+                        // index far outside [0, extent - 1), so the test catches every sample off the box
+                        const unsigned ix = (unsigned)(__float_as_int(tx) - 0x4B400000);
+                        const unsigned iy = (unsigned)(__float_as_int(ty) - 0x4B400000);
+                        const unsigned iz = (unsigned)(__float_as_int(tz) - 0x4B400000);
+                        if (ix >= (unsigned)(BF - 1) || iy >= (unsigned)(BS - 1) || iz >= (unsigned)(BZb - 1)) {
                             atomicAdd(p.flags + FLAG_SLAB_OUT_OF_BOX, 1);
                             acc += trilerp_zero(vb, p.vol, (yt ? qy : qx) + (float)sb.lo[0],
                                                 (yt ? qx : qy) + (float)sb.lo[1], qz + (float)sb.lo[2]);

@@ -199,6 +199,52 @@ def test_slab_adjoint_box_pitch(ops, case, pitch):
     assert g.read_flags()[:4] == [0, 0, 0, 0]
 
 
+def test_extreme_fan_direct_rays(ops):
+    """A ~160-degree fan (source 20 mm from the centre of a 16 mm volume, 61 columns of 5 mm pixels 30 mm
+    from the source, views every 45 degrees): in the views along the axes the central pixel column looks
+    exactly across one axis, and a detector tile (16 columns for the projector, 32 for the adjoint) spreads
+    its rays by more than 45 degrees, so that column's rays barely advance along their tile's march axis
+    while crossing the volume. Both the slab-staged projector and adjoint route them through their
+    direct global-memory paths (flag 1, set by each); FP, matched adjoint and BP match the oracle. The
+    tiles' slab boxes, built from their corner rays, do not bound such rays, so the sample loops' exact
+    per-axis box tests are exercised too."""
+    kw = dict(vol_shape=(16, 16, 16), vol_spacing=(1.0, 1.0, 1.0), det_shape=(16, 61), det_spacing=(2.5, 5.0),
+              views=8, range=2 * math.pi, sid=20.0, sdd=30.0)
+    args = (kw["vol_shape"], kw["vol_spacing"], kw["det_shape"], kw["det_spacing"], kw["views"], kw["range"],
+            kw["sid"], kw["sdd"])
+    g = ops.Geometry.cone_circular(*args)
+    og = oracle.cone_circular(*args)
+    x = inputs.uniform(og.vol_shape, seed=71)
+    g.set_variant(0, 3)
+    g.set_variant(1, 3)
+    g.read_flags(reset=True)
+    p = host(ops.forward_project(to_dev(x), g))
+    assert rel_l2(p, oracle.fp(og, x)) <= 1e-5
+    assert g.read_flags(reset=True)[1] > 0
+    y = inputs.gaussian(og.sino_shape, seed=72)
+    a = host(ops.adjoint(to_dev(y), g))
+    assert rel_l2(a, oracle.adjoint(og, y)) <= 1e-5
+    assert g.read_flags()[1] > 0
+    for w in (0, 1):
+        b = host(ops.back_project(to_dev(y), g, w))
+        assert rel_l2(b, oracle.bp(og, y, w)) <= 1e-5
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_extreme_fan_other_variants(ops, variant):
+    """The extreme-fan geometry through the other projector variants (1 one thread per ray, 2 thread-staged
+    slabs) and adjoint variants (1 atomic scatter, 2 output-stationary bricks): all match the oracle."""
+    args = ((16, 16, 16), (1.0, 1.0, 1.0), (16, 61), (2.5, 5.0), 8, 2 * math.pi, 20.0, 30.0)
+    g = ops.Geometry.cone_circular(*args)
+    og = oracle.cone_circular(*args)
+    g.set_variant(0, variant)
+    g.set_variant(1, variant)
+    x = inputs.uniform(og.vol_shape, seed=73)
+    assert rel_l2(host(ops.forward_project(to_dev(x), g)), oracle.fp(og, x)) <= 1e-5
+    y = inputs.gaussian(og.sino_shape, seed=74)
+    assert rel_l2(host(ops.adjoint(to_dev(y), g)), oracle.adjoint(og, y)) <= 1e-5
+
+
 def test_slab_adjoint_dense_rays_keep_fp32_boxes(ops):
     """Detector pixels much smaller than the voxels (many rays per voxel support): the bound on the
     box values exceeds the fixed-point budget and the boxes stay FP32; the operator is unchanged."""
