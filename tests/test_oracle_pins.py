@@ -329,13 +329,17 @@ def test_cone_fp_converges_to_ellipsoid_chords(oracle_lib):
     assert errs[1] < 0.7 * errs[0], errs
 
 
-@pytest.mark.parametrize("case", ["fan", "parallel", "cone"])
+@pytest.mark.parametrize("case", ["fan", "parallel", "cone", "cone_wide_fan"])
 def test_brute_force_system_matrix(oracle_lib, case):
     o = oracle_lib
     if case == "fan":
         g = o.fan_circular((8, 8), (1.0, 1.1), 11, 1.7, 6, 2 * math.pi, 20.0, 35.0)
     elif case == "parallel":
         g = o.parallel2d((8, 7), (1.0, 1.2), 11, 1.1, 6, math.pi, det_offset=0.21)
+    elif case == "cone_wide_fan":
+        # ~100-degree fan (source 8 mm from the centre of a 6 mm volume, 3 mm pixels 12 mm away): the
+        # regime of the GPU's extreme-fan tests, pinned here by the explicit matrix
+        g = o.cone_circular((6, 6, 6), (1.0, 1.0, 1.0), (5, 9), (2.0, 3.0), 4, 2 * math.pi, 8.0, 12.0)
     else:
         g = o.cone_circular((6, 6, 6), (1.0, 0.9, 1.2), (5, 7), (1.6, 1.5), 4, 2 * math.pi, 25.0, 40.0,
                             det_offset=(0.3, -0.2))
