@@ -73,6 +73,8 @@ def test_fp_matches_oracle(ops, case, variant):
     assert g.read_flags()[:4] == [0, 0, 0, 0]
 
 
+YFAN = Case("fan_extreme", dict(kind="fan2d"), 2)   # only its ndim is used (sinogram reshaping)
+
 # y and x extents of 16-byte multiples in FP32 and BF16, so that x-march boxes of the TMA-staged
 # projector can come from the y-fastest copy of the volume; ragged detector, offsets
 YFAST = Case("cone_y_fastest", dict(kind="cone", vol_shape=(22, 24, 32), vol_spacing=(0.5, 0.45, 0.5),
@@ -243,6 +245,27 @@ def test_extreme_fan_other_variants(ops, variant):
     assert rel_l2(host(ops.forward_project(to_dev(x), g)), oracle.fp(og, x)) <= 1e-5
     y = inputs.gaussian(og.sino_shape, seed=74)
     assert rel_l2(host(ops.adjoint(to_dev(y), g)), oracle.adjoint(og, y)) <= 1e-5
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_extreme_fan_2d(ops, variant):
+    """2D fan beam with a ~160-degree fan (source 20 mm from the centre of a 16 mm image, 61 bins of 5 mm
+    30 mm away): every projector and adjoint variant matches the oracle, and so does the BP."""
+    args = ((16, 16), (1.0, 1.0), 61, 5.0, 8, 2 * math.pi, 20.0, 30.0)
+    g = ops.Geometry.fan2d(*args)
+    og = oracle.fan_circular(*args)
+    g.set_variant(0, variant)
+    g.set_variant(1, variant)
+    x = inputs.uniform(og.vol_shape, seed=75).reshape(16, 16)
+    p = host(ops.forward_project(to_dev(x), g))
+    assert rel_l2(sino3(YFAN, p), oracle.fp(og, x.reshape(og.vol_shape))) <= 1e-5
+    y = inputs.gaussian(og.sino_shape, seed=76)
+    a = host(ops.adjoint(to_dev(y.reshape(og.n_views, -1)), g))
+    ref = oracle.adjoint(og, y)
+    assert rel_l2(a.reshape(ref.shape), ref) <= 1e-5
+    b = host(ops.back_project(to_dev(y.reshape(og.n_views, -1)), g, 0))
+    refb = oracle.bp(og, y, 0)
+    assert rel_l2(b.reshape(refb.shape), refb) <= 1e-5
 
 
 def test_slab_adjoint_dense_rays_keep_fp32_boxes(ops):
