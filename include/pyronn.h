@@ -155,7 +155,9 @@ PYRONN_API int pyronn_geom_count_samples(pyronn_geom_t g, int64_t *total);
 
 /* Forward projection (Sec. 2.1 ray-driven; operator A of Sec. 2.2): sino = A vol, overwriting
  * sino. The TMA-staged projector may first copy the volume into a geometry-owned y-fastest buffer
- * (allocated on first use; see PYRONN_TUNE_FP_TRANSPOSE). */
+ * (allocated on first use; see PYRONN_TUNE_FP_TRANSPOSE); since that buffer belongs to the
+ * geometry, forward projections with one geometry on different streams must not overlap (use one
+ * geometry per stream, or a plan, whose copies are per volume). */
 PYRONN_API int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, void *stream);
 
 /* Matched adjoint (operator A^T of Sec. 2.2, the exact transpose of pyronn_fp):
