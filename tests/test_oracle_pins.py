@@ -212,6 +212,22 @@ def test_positions_equal_circular_and_normalisation(oracle_lib):
     assert np.allclose(g3.views, g1.views, rtol=1e-12, atol=1e-14)
 
 
+def test_helical_orbit_advance_and_centring(oracle_lib):
+    """Helical orbit (pitch h): the source and detector centre rise by h per full turn, linearly in the
+    view index, the trajectory is centred on z = 0, and the in-plane frames equal the circular ones."""
+    o = oracle_lib
+    V, rng_, sid, sdd, h = 30, 4 * math.pi, 600.0, 1000.0, 7.5
+    src, det, eu, ev = o.circular_frames(V, rng_, sid, sdd, h)
+    src0, det0, eu0, ev0 = o.circular_frames(V, rng_, sid, sdd, 0.0)
+    rise = h * (rng_ / V) / (2 * math.pi)            # pitch x fraction of a turn per view
+    assert np.allclose(np.diff(src[:, 2]), rise, rtol=0, atol=1e-12)
+    assert abs(src[:, 2].mean()) < 1e-12
+    assert abs(src[-1, 2] - src[0, 2] - h * (V - 1) / V * 2) < 1e-12      # two turns, V - 1 steps
+    assert np.array_equal(det[:, 2], src[:, 2])
+    assert np.allclose(src[:, :2], src0[:, :2], atol=0) and np.allclose(det[:, :2], det0[:, :2], atol=0)
+    assert np.array_equal(eu, eu0) and np.array_equal(ev, ev0)
+
+
 # ------------------------------------------------------------------------------------------------
 # forward projection pins (Sec. 2.1)
 # ------------------------------------------------------------------------------------------------
@@ -281,6 +297,41 @@ def test_parallel_symmetry(oracle_lib):
     f = inputs.rasterise_ellipses(inputs.random_ellipses(6, 9.0, seed=8), (21, 19), (1.0, 0.9))
     p = o.fp(g, f)[:, 0, :]
     assert np.max(np.abs(p[V // 2:] - p[:V // 2, ::-1])) < 1e-12 * np.abs(p).max()
+
+
+def test_volume_offset_is_a_world_translation(oracle_lib):
+    """Moving the volume centre to o and the source and detector by the same o changes nothing: FP,
+    matched adjoint and the weighted BP of an offset volume equal those of the centred volume seen
+    from the source and detector translated by -o. This fixes where the offset enters the voxel
+    centres, the sample positions and the ray's reference point (the point closest to the volume
+    centre, which sets the sampling phase)."""
+    o = oracle_lib
+    rng = np.random.default_rng(8)
+    shape, sp, off = (6, 7, 8), (0.9, 0.7, 0.8), (2.3, -4.1, 3.7)        # (z, y, x)
+    oxyz = np.array([off[2], off[1], off[0]])
+    V = 5
+    src, det, eu, ev = o.circular_frames(V, 2 * math.pi, 40.0, 70.0)
+    src, det = src + oxyz, det + oxyz          # the orbit follows the volume
+    g1 = o.cone_from_positions(shape, sp, (9, 11), (0.9, 0.8), src, det, eu, ev, vol_offset=off)
+    g0 = o.cone_from_positions(shape, sp, (9, 11), (0.9, 0.8), src - oxyz, det - oxyz, eu, ev)
+    f = rng.random(shape)
+    y = rng.random(g1.sino_shape)
+    p1, p0 = o.fp(g1, f), o.fp(g0, f)
+    assert p0.max() > 1.0 and rel_l2(p1, p0) < 1e-12
+    assert rel_l2(o.adjoint(g1, y), o.adjoint(g0, y)) < 1e-12
+    assert rel_l2(o.bp(g1, y, 1), o.bp(g0, y, 1)) < 1e-12
+    # 2D parallel beam: the detector line through o instead of through the origin
+    t = 0.4
+    base = np.array([0, 0, 0, -math.sin(t), math.cos(t), 0, 0, 0, 1, -math.cos(t), -math.sin(t), 0])
+    moved = base.copy()
+    moved[0:3] = (oxyz[0], oxyz[1], 0.0)
+    h1 = o.parallel_from_views((1, 7, 8), (1.0, 0.7, 0.8), (1, 13), (1.0, 0.6), [moved],
+                               vol_offset=(0.0, off[1], off[2]), ndim=2)
+    h0 = o.parallel_from_views((1, 7, 8), (1.0, 0.7, 0.8), (1, 13), (1.0, 0.6), [base], ndim=2)
+    f2 = rng.random((1, 7, 8))
+    q2 = rng.random(h1.sino_shape)
+    assert o.fp(h0, f2).max() > 1.0 and rel_l2(o.fp(h1, f2), o.fp(h0, f2)) < 1e-12
+    assert rel_l2(o.bp(h1, q2), o.bp(h0, q2)) < 1e-12
 
 
 def test_fp_converges_to_ellipse_chords(oracle_lib):
@@ -429,6 +480,41 @@ def test_bp_single_pixel_footprint(oracle_lib):
     assert np.allclose(b, expect, atol=1e-12)
 
 
+def test_bp_voxels_behind_the_source_receive_nothing(oracle_lib):
+    """Source inside the volume (sid 2.5 mm, voxels at x = -4 ... 4 mm): one view, an all-ones
+    sinogram. A voxel in front of the source gets the bilinear interpolant of the ones (zero outside
+    the detector) at its independently intersected (u, v), times 1 / w^2 in the weighted mode; a voxel
+    behind the source plane, whose central projection lands on the detector through the source, gets
+    nothing."""
+    o = oracle_lib
+    sid, sdd, nv, nu, dv, du = 2.5, 10.0, 31, 41, 1.0, 1.0
+    g = o.cone_circular((5, 9, 9), (1.0, 1.0, 1.0), (nv, nu), (dv, du), 1, 2 * math.pi, sid, sdd)
+    q = np.ones(g.sino_shape)
+    Xs = voxel_centres(g.vol_shape, g.vol_spacing)
+    S, Dc, eu, ev = circ_frame(0.0, sid, sdd)
+    axis = (Dc - S) / np.linalg.norm(Dc - S)
+
+    def ones_interp(s, n):
+        return sum(hat(s - m) for m in range(n))
+
+    for weight in (0, 1):
+        b = o.bp(g, q, weight)
+        n_behind = n_front = 0
+        for idx in np.ndindex(*g.vol_shape):
+            X = Xs[idx]
+            if np.dot(X - S, axis) <= 0:
+                assert b[idx] == 0.0
+                u, v, _ = detector_coords(X, S, Dc, eu, ev, nu, nv, du, dv)
+                n_behind += ones_interp(u, nu) * ones_interp(v, nv) > 0.5
+                continue
+            u, v, w = detector_coords(X, S, Dc, eu, ev, nu, nv, du, dv)
+            expect = ones_interp(u, nu) * ones_interp(v, nv) * (1.0 / (w * w) if weight else 1.0)
+            n_front += expect > 0
+            assert abs(b[idx] - expect) < 1e-12 * max(1.0, expect)
+        # the case is live: behind-source voxels that would land on the detector, and lit voxels in front
+        assert n_behind > 10 and n_front > 100
+
+
 def test_parallel_bp_constant_along_rays(oracle_lib):
     o = oracle_lib
     g = o.parallel2d((9, 12), (1.0, 1.0), 15, 1.0, 1)
@@ -440,6 +526,26 @@ def test_parallel_bp_constant_along_rays(oracle_lib):
     for j in range(9):
         u = (j - 4) + 7
         assert abs(b[j, 0] - q[0, 0, u]) < 1e-14
+
+
+def test_parallel_bp_detector_offset(oracle_lib):
+    """Parallel beam with the detector shifted by ou along eu: a voxel at signed distance s along eu
+    reads bin (s - ou) / du + (Nu - 1) / 2, at t = 0 (s = y) and at an oblique angle."""
+    o = oracle_lib
+    ny, nx, nu, du, ou = 9, 12, 19, 0.8, 1.37
+    for t in (0.0, 0.7):
+        view = [0, 0, 0, -math.sin(t), math.cos(t), 0, 0, 0, 1, -math.cos(t), -math.sin(t), 0]
+        g = o.parallel_from_views((1, ny, nx), (1.0, 1.0, 1.0), (1, nu), (1.0, du), [view], det_offset=(0.0, ou),
+                                  ndim=2)
+        q = np.random.default_rng(4).random(g.sino_shape)
+        b = o.bp(g, q)[0]
+        Xs = voxel_centres(g.vol_shape, g.vol_spacing)[0]
+        for j in range(ny):
+            for i in range(nx):
+                s_ = Xs[j, i, 0] * -math.sin(t) + Xs[j, i, 1] * math.cos(t)
+                uc = (s_ - ou) / du + (nu - 1) / 2
+                expect = sum(q[0, 0, m] * hat(uc - m) for m in range(nu))
+                assert abs(b[j, i] - expect) < 1e-13
 
 
 # ------------------------------------------------------------------------------------------------
