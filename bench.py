@@ -183,6 +183,33 @@ def oracle_sample_rate(vol, n_views: int, target_s: float = 10.0):
     return samples / dt / 1e9, samples, dt, threads, nv
 
 
+def oracle_single_core_rate(vol):
+    """The FP64 oracle on one thread: forward projection of one view of the workload (a few seconds).
+    Returns (G samples/s, samples, seconds)."""
+    import oracle
+    og = oracle.cone_circular((256, 256, 256), (0.5, 0.5, 0.5), (512, 512), (0.6, 0.6), 360, 2 * math.pi,
+                              750.0, 1200.0)
+    g = oracle.Geometry(og.vol_shape, og.vol_spacing, og.vol_offset, og.det_shape, og.det_spacing, og.det_offset,
+                        1, og.views[[3]], og.dt)
+    v = np.ascontiguousarray(vol, dtype=np.float64)
+    n_all = oracle.max_threads()
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.fp(g, v)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(n_all)
+    samples = int(oracle.count_samples(g).sum())
+    return samples / dt / 1e9, samples, dt
+
+
+def single_core_entry(vol):
+    rate, s, dt = oracle_single_core_rate(vol)
+    return {"value": rate, "unit": "G ray-samples/s", "cores": 1,
+            "sample": f"FP64 oracle forward projection of 1 of 360 views on one thread ({s} samples, {dt:.1f} s)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -203,7 +230,8 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(WORKLOAD, kernel="FP64 CPU oracle, forward projection"),
             "cpu_baseline": {"value": value, "unit": "G ray-samples/s", "cores": threads, "kind": "oracle",
-                             "sample": f"forward projection of {nv} views per step (of 360), full detector"},
+                             "sample": f"forward projection of {nv} views per step (of 360), full detector",
+                             "single_core": single_core_entry(vol)},
             "e2e": {"value": value, "unit": "G ray-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -496,7 +524,8 @@ def run_gpu(args):
         rate, s, dt, threads, nv = oracle_sample_rate(vol_np, 64, target_s=args.ref_seconds)
         result["cpu_baseline"] = {"value": rate, "unit": "G ray-samples/s", "cores": threads, "kind": "oracle",
                                   "sample": f"FP64 oracle forward projection of {nv} of 360 views, full detector "
-                                            f"({s} samples, {dt:.1f} s)"}
+                                            f"({s} samples, {dt:.1f} s)",
+                                  "single_core": single_core_entry(vol_np)}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
