@@ -5,7 +5,9 @@ term, a wrong sign or index, a transposed operand, a half-voxel offset, a wrong 
 compiles the copy with the oracle's own build step into a temporary library, loads a second
 instance of the oracle's Python wrapper on it and runs the pins named beside the mistake: every one
 of them must fail. A copy without a planted mistake, built and loaded the same way, passes all of
-them. The oracle itself is never modified; everything happens on the CPU.
+them. The acquisition-artifact references (oracle/artifacts.py) get the same treatment against
+their pin, from a copy of the module loaded under another name. The oracle itself is never
+modified; everything happens on the CPU.
 """
 import importlib.util
 import os
@@ -107,6 +109,25 @@ MUTANTS = [
 ]
 
 
+# the same for the acquisition-artifact references (oracle/artifacts.py, Sec. 2.4); the pin is
+# check_artifact_references
+ARTIFACT_MUTANTS = [
+    ("row jitter shifts the wrong way", "src = u - int(s[n, v])", "src = u + int(s[n, v])"),
+    ("column jitter shifts the wrong way", "src = v - int(s[n, u])", "src = v + int(s[n, u])"),
+    ("noise without the mean", "+ mean + std * np.asarray(noise", "+ std * np.asarray(noise"),
+    ("noise scaled by the variance", "std * np.asarray(noise, dtype=np.float64)",
+     "std * std * np.asarray(noise, dtype=np.float64)"),
+    ("ring gain added instead of multiplied", "*= float(gain)", "+= float(gain)"),
+    ("ring view range includes its end", "out[view_begin:view_end, :, int(c)]",
+     "out[view_begin:view_end + 1, :, int(c)]"),
+    ("blur kernel not centred", "t = j - 0.5 * (length - 1)", "t = j - 0.5 * length"),
+    ("blur along the mirrored angle", "v + t * sa)", "v - t * sa)"),
+    ("blur weight 1 / (L - 1)", "out[n, v, u] = acc / length", "out[n, v, u] = acc / max(length - 1, 1)"),
+    ("blur bilinear weights swapped in v", "for dy, wy in ((0, 1.0 - fy), (1, fy)):",
+     "for dy, wy in ((0, fy), (1, 1.0 - fy)):"),
+]
+
+
 def _load_copy(name, src_text, tmp):
     """A second instance of the oracle wrapper whose library is built from src_text."""
     init = os.path.join(os.path.dirname(oracle.__file__), "__init__.py")
@@ -153,3 +174,19 @@ def test_planted_mistake_fails_its_pins(copies, label):
     for pin in pins_for:
         with pytest.raises(AssertionError):
             _run_pin(pin, copies[label])
+
+
+@pytest.mark.parametrize("label", [m[0] for m in ARTIFACT_MUTANTS])
+def test_planted_artifact_mistake_fails_its_pin(tmp_path, label):
+    from oracle import artifacts
+    with open(artifacts.__file__) as f:
+        src = f.read()
+    i, (_, old, new) = next((i, m) for i, m in enumerate(ARTIFACT_MUTANTS) if m[0] == label)
+    assert src.count(old) == 1, f"{label}: the original text must occur exactly once"
+    path = tmp_path / f"artifacts_mutant_{i}.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location(f"artifacts_mutant_{i}", str(path))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with pytest.raises(AssertionError):
+        pins.check_artifact_references(mod)

@@ -662,11 +662,17 @@ def test_fdk_cosine_weight_from_independent_geometry(oracle_lib):
 # ------------------------------------------------------------------------------------------------
 
 def test_artifact_references():
-    """Jitter by zero is the identity and by s moves every value s pixels (zero fill); ring gains touch
-    only the chosen columns and views; the blur kernel has unit weight (interior sums preserved),
-    blurs a point into a segment of L pixels of weight 1/L along the view angle (u at 0, v at pi/2),
-    and L = 1 is the identity."""
-    from oracle import artifacts as A
+    from oracle import artifacts
+    check_artifact_references(artifacts)
+
+
+def check_artifact_references(A):
+    """Jitter by zero is the identity and by s moves every value s pixels (zero fill); noise adds mean
+    plus std times the sample; ring gains touch only the chosen columns and views; the blur kernel has
+    unit weight (interior sums preserved), blurs a point into a segment of L pixels of weight 1/L along
+    the view angle (u at 0, v at pi/2, the diagonal at pi/4), leaves a linear ramp unchanged away from
+    the edges at any angle (a symmetric average of a linear function, sampled bilinearly, is its
+    centre value), and L = 1 is the identity."""
     rng = np.random.default_rng(0)
     p = rng.random((3, 9, 11))
     assert np.array_equal(A.detector_jitter(p, np.zeros((3, 9), int), 0), p)
@@ -688,3 +694,19 @@ def test_artifact_references():
     assert np.allclose(b[1][:, 7], row) and np.allclose(b[1].sum(), 1.0)
     b = A.motion_blur(d, [0.7, 2.1], 4)
     assert np.allclose(b.sum(axis=(1, 2)), 1.0)
+    # pi / 4, L = 3 (t = -1, 0, 1): only t = -1 from (8, 8) and t = 1 from (6, 6) reach the point, each
+    # with bilinear weight (1 / sqrt 2)^2 = 1/2; at (7, 7) t = 0 hits it and t = +-1 each add
+    # (1 - 1 / sqrt 2)^2; the anti-diagonal neighbours get nothing
+    b = A.motion_blur(d[:1], [math.pi / 4], 3)[0]
+    assert abs(b[8, 8] - 1 / 6) < 1e-12 and abs(b[6, 6] - 1 / 6) < 1e-12
+    assert abs(b[7, 7] - (1 + 2 * (1 - 1 / math.sqrt(2)) ** 2) / 3) < 1e-12
+    assert b[6, 8] == 0.0 and b[8, 6] == 0.0
+    vv, uu = np.meshgrid(np.arange(15.0), np.arange(15.0), indexing="ij")
+    ramp = np.broadcast_to(0.3 * uu - 0.7 * vv + 2.0, (3, 15, 15))
+    b = A.motion_blur(ramp, [0.4, 1.9, 3.5], 5)
+    assert np.allclose(b[:, 3:12, 3:12], ramp[:, 3:12, 3:12], rtol=0, atol=1e-12)
+    z = rng.standard_normal(p.shape)
+    assert np.allclose(A.gaussian_noise(p, np.zeros_like(p), 0.25, 3.0), p + 0.25, rtol=0, atol=1e-15)
+    assert np.allclose(A.gaussian_noise(p, z, 0.0, 2.0) - p, 2.0 * z, rtol=0, atol=1e-14)
+    r = A.ring_artifacts(p, [4], [0.5], 0, 2)
+    assert np.allclose(r[:2, :, 4], 0.5 * p[:2, :, 4]) and np.array_equal(r[2], p[2])
