@@ -70,7 +70,11 @@ typedef enum { PYRONN_F32 = 0, PYRONN_BF16 = 1, PYRONN_F16 = 2 } pyronn_dtype;
 typedef enum { PYRONN_BP_PLAIN = 0, PYRONN_BP_INV_W2 = 1 } pyronn_bp_weight;
 
 /* Volume description: the paper's volume_shape / volume_spacing (Listing 1), numpy (z, y, x)
- * order. ndim = 2 describes an image: shape[0] must be 1, spacing[0] and offset[0] are ignored. */
+ * order. ndim = 2 describes an image: shape[0] must be 1, spacing[0] and offset[0] are ignored.
+ * The create calls return PYRONN_INVALID_ARG for a shape outside [1, 16384], an offset that is not
+ * finite, a spacing (here or on the detector) that is not positive or whose value or reciprocal is
+ * not finite in FP32, a geometry whose FP32 per-view tables would hold a non-finite entry, or a
+ * default step (half the smallest spacing) that gives more than 2^22 samples across the volume. */
 typedef struct {
     int ndim;
     int shape[3];        /* (Nz, Ny, Nx) */
@@ -133,7 +137,10 @@ PYRONN_API int pyronn_geom_create_matrices2d(const pyronn_vol_desc *vol, const p
 
 PYRONN_API int pyronn_geom_destroy(pyronn_geom_t g);
 
-/* Sampling step along rays in mm (> 0). Default: half the smallest voxel spacing. */
+/* Sampling step along rays in mm (> 0). Default: half the smallest voxel spacing. PYRONN_INVALID_ARG
+ * if the step or its reciprocal is not finite in FP32, or if the diagonal of the support box
+ * ((-1, N) voxels on every axis) spans more than 2^22 steps. Steps of 2^16 voxels or more are accepted
+ * and run on the direct projector and the brick adjoint (the slab-staged kernels need fewer). */
 PYRONN_API int pyronn_geom_set_step(pyronn_geom_t g, double dt_mm);
 PYRONN_API int pyronn_geom_get_step(pyronn_geom_t g, double *dt_mm);
 

@@ -71,6 +71,26 @@ void cross(const double a[3], const double b[3], double o[3]) {
 
 double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
+// The device tables hold spacings and their reciprocals in FP32.
+bool fp32_spacing(double s) {
+    return s > 0 && std::isfinite((float)s) && (float)s > 0.0f && std::isfinite((float)(1.0 / s));
+}
+
+// Sample indices and counts stay far inside 32-bit and FP32-exact ranges: the diagonal of the support
+// box ((-1, N) on every axis) spans at most 2^22 steps; the step and its reciprocal are finite in FP32.
+int check_step(const pyronn_geom *g, double dt) {
+    if (!(dt > 0) || !std::isfinite((float)dt) || !std::isfinite((float)(1.0 / dt)))
+        return set_error(PYRONN_INVALID_ARG, "step %g mm must be positive, with it and its reciprocal finite in FP32",
+                         dt);
+    const double ex = (g->nx + 1) * g->sx, ey = (g->ny + 1) * g->sy;
+    const double ez = g->ndim == 3 ? (g->nz + 1) * g->sz : 0.0;
+    const double diag = std::sqrt(ex * ex + ey * ey + ez * ez);
+    if (!(diag / dt <= 4194304.0))
+        return set_error(PYRONN_INVALID_ARG, "step %g mm: the volume's diagonal (%g mm) spans more than 2^22 steps",
+                         dt, diag);
+    return PYRONN_OK;
+}
+
 int check_descs(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_views, int want_ndim) {
     if (!vol || !det) return set_error(PYRONN_INVALID_ARG, "null descriptor");
     if (vol->ndim != 2 && vol->ndim != 3) return set_error(PYRONN_INVALID_ARG, "vol.ndim must be 2 or 3");
@@ -80,14 +100,19 @@ int check_descs(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_vi
         if (vol->shape[i] < 1 || vol->shape[i] > 16384)
             return set_error(PYRONN_INVALID_ARG, "vol.shape[%d] = %d out of range [1, 16384]", i, vol->shape[i]);
     if (vol->ndim == 2 && vol->shape[0] != 1) return set_error(PYRONN_INVALID_ARG, "2D volume needs shape[0] == 1");
-    for (int i = (vol->ndim == 2 ? 1 : 0); i < 3; ++i)
-        if (!(vol->spacing[i] > 0) || !std::isfinite(vol->spacing[i]))
-            return set_error(PYRONN_INVALID_ARG, "vol.spacing[%d] must be positive", i);
+    for (int i = (vol->ndim == 2 ? 1 : 0); i < 3; ++i) {
+        if (!fp32_spacing(vol->spacing[i]))
+            return set_error(PYRONN_INVALID_ARG, "vol.spacing[%d] must be positive, with it and its reciprocal "
+                             "finite in FP32", i);
+        if (!std::isfinite(vol->offset[i])) return set_error(PYRONN_INVALID_ARG, "vol.offset[%d] must be finite", i);
+    }
     for (int i = 0; i < 2; ++i) {
         if (det->shape[i] < 1 || det->shape[i] > 65536)
             return set_error(PYRONN_INVALID_ARG, "det.shape[%d] = %d out of range", i, det->shape[i]);
-        if (!(det->spacing[i] > 0) || !std::isfinite(det->spacing[i]))
-            return set_error(PYRONN_INVALID_ARG, "det.spacing[%d] must be positive", i);
+        if (!fp32_spacing(det->spacing[i]))
+            return set_error(PYRONN_INVALID_ARG, "det.spacing[%d] must be positive, with it and its reciprocal "
+                             "finite in FP32", i);
+        if (!std::isfinite(det->offset[i])) return set_error(PYRONN_INVALID_ARG, "det.offset[%d] must be finite", i);
     }
     if (vol->ndim == 2 && det->shape[0] != 1) return set_error(PYRONN_INVALID_ARG, "2D detector needs shape[0] == 1");
     if (n_views < 1 || n_views > (1 << 20)) return set_error(PYRONN_INVALID_ARG, "n_views = %d out of range", n_views);
@@ -224,6 +249,7 @@ int ensure_fbp(pyronn_geom *g) {
 }
 
 int finalize_geometry(pyronn_geom *g) {
+    if (int rc = check_step(g, g->dt)) return rc;
     const int V = g->n_views;
     g->fp_rec.assign(V, FpRec{});
     g->bp_rec.assign(V, BpRec{});
@@ -303,6 +329,15 @@ int finalize_geometry(pyronn_geom *g) {
             f.B0[i] = (float)B0[i]; f.Bu[i] = (float)Bu[i]; f.Bv[i] = (float)Bv[i];
         }
         for (int i = 0; i < 12; ++i) g->bp_rec[n].P[i] = (float)Pc[i];
+        bool finite = true;
+        for (int i = 0; i < 3; ++i)
+            finite = finite && std::isfinite(f.R0[i]) && std::isfinite(f.Ru[i]) && std::isfinite(f.Rv[i]) &&
+                     std::isfinite(f.B0[i]) && std::isfinite(f.Bu[i]) && std::isfinite(f.Bv[i]);
+        for (int i = 0; i < 12; ++i) finite = finite && std::isfinite(g->bp_rec[n].P[i]);
+        for (int i = 0; i < VIEW64_STRIDE; ++i) finite = finite && std::isfinite(g->views_ext[(size_t)n * VIEW64_STRIDE + i]);
+        if (!finite)
+            return set_error(PYRONN_INVALID_ARG, "view %d: the geometry does not fit the FP32 device tables "
+                             "(a non-finite entry)", n);
     }
     g->sample_count = -1;
     g->fp_cfg_ready = 0;
@@ -577,7 +612,7 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
 int pyronn_geom_set_step(pyronn_geom_t g, double dt_mm) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
-    if (!(dt_mm > 0) || !std::isfinite(dt_mm)) return set_error(PYRONN_INVALID_ARG, "step must be positive");
+    if (int rc = check_step(g, dt_mm)) return rc;
     g->dt = dt_mm;
     g->sample_count = -1;
     g->fp_cfg_ready = 0;
@@ -679,10 +714,10 @@ int pyronn_geom_count_samples(pyronn_geom_t g, int64_t *total) {
                         hi = std::min(hi, std::max(t1, t2));
                     }
                     if (empty || !(hi > lo)) continue;
-                    // integers k with lo < (k + 1/2) dt < hi
-                    long long k0 = (long long)std::floor(lo / dt - 0.5) + 1;
-                    long long k1 = (long long)std::ceil(hi / dt - 0.5) - 1;
-                    if (k1 >= k0) local += k1 - k0 + 1;
+                    // integers k with lo < (k + 1/2) dt < hi; hi - lo is at most the support box's
+                    // diagonal, at most 2^22 steps, so the count is exact in double
+                    const double k0 = std::floor(lo / dt - 0.5) + 1, k1 = std::ceil(hi / dt - 0.5) - 1;
+                    if (k1 >= k0) local += (long long)(k1 - k0 + 1);
                 }
         }
         sum.fetch_add(local);

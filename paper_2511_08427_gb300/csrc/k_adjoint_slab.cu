@@ -870,11 +870,14 @@ long long as_tile_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0
                     }
                 }
             long long e[3];
+            bool bounded = true;
             for (int a = 0; a < 3; ++a) {
                 if (a == m) e[a] = D + 2 * G + 1;
-                else e[a] = (long long)std::ceil(mx[a] - mn[a]) + 5;
+                else e[a] = box_extent(mx[a] - mn[a], 5, dims[a] + 2 * G + 2);
+                bounded = bounded && e[a] >= 0;
                 e[a] = std::min<long long>(e[a], dims[a] + 2 * G + 2);
             }
+            if (!bounded) continue;
             e[0] = ((e[0] + 3 + 3) / 4) * 4;   // x start rounded down (<= 3 more), extent rounded up
             if (m == 0 && xpad) e[0] += 1;         // odd row pitch of x-march boxes
             best = std::max(best, e[0] * e[1] * e[2]);
@@ -919,6 +922,7 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     if (g->ndim != 3) return c;
     const int nmax = std::max(g->nx, std::max(g->ny, g->nz));
     const double smin = std::min(g->sx, std::min(g->sy, g->sz));
+    if (!(g->dt / smin < 65535.0)) return c;   // steps of 2^16 voxels or more: the brick adjoint
     c.guard = 1 + (int)std::floor(g->dt / smin);
     // two CTAs per SM: 224 KB of the SM's shared memory, 1 KB reserved per CTA, the static tile
     // state (the occupancy calculator on GB300 admits two CTAs of 114264 bytes each, not of 115152)

@@ -243,9 +243,9 @@ long long tile_box_bound(const pyronn_geom *g, const FpRec &rec, int tu0, int tv
                     mn1 = std::min(mn1, q1); mx1 = std::max(mx1, q1);
                     mn2 = std::min(mn2, q2); mx2 = std::max(mx2, q2);
                 }
-            long long e1 = (long long)std::ceil(mx1 - mn1) + 6, e2 = (long long)std::ceil(mx2 - mn2) + 6;
-            e1 = std::min<long long>(e1, dims[a1] + 2 * G + 2);
-            e2 = std::min<long long>(e2, dims[a2] + 2 * G + 2);
+            const long long e1 = box_extent(mx1 - mn1, 6, dims[a1] + 2 * G + 2);
+            const long long e2 = box_extent(mx2 - mn2, 6, dims[a2] + 2 * G + 2);
+            if (e1 < 0 || e2 < 0) continue;
             long long em = std::min<long long>(D + 2 * G + 1, Nm + 2 * G + 2);
             best = std::max(best, em * e1 * e2);
         }
@@ -262,6 +262,9 @@ FpSlabCfg choose_fp_slab_cfg(const pyronn_geom *g) {
     cfg.depth = 8;
     double smin = std::min(g->sx, std::min(g->sy, g->sz));
     double step_max = g->dt / smin;   // largest per-sample advance along any axis, in voxels
+    // steps of 2^16 voxels or more (at most one sample per ray) go to the generic kernel; this keeps
+    // the guard and the box arithmetic below in range
+    if (!(step_max < 65535.0)) return cfg;
     cfg.guard = 1 + (int)std::floor(step_max);
     const int ntu = (g->nu + cfg.tu - 1) / cfg.tu, ntv = (g->nv + cfg.tv - 1) / cfg.tv;
     std::atomic<int> next(0);

@@ -531,11 +531,12 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
     FpTmaBox c{};
     const int align = 16 / (int)elem;
     if (((size_t)g->nx * elem) % 16 != 0) return c;
+    const double smin = std::min(g->sx, std::min(g->sy, g->sz));
+    if (!(g->dt / smin < 65535.0)) return c;   // steps of 2^16 voxels or more: another kernel
     c.xt = xt && ((size_t)g->ny * elem) % 16 == 0;
     // slab depth: a multiple of the x alignment so that x-march boxes start aligned
     c.depth = depth > 0 ? ((depth + align - 1) / align) * align : 8;
     c.nbuf = nbuf == 2 ? 2 : 1;   // default: one buffer (more CTAs per SM beat the copy overlap)
-    double smin = std::min(g->sx, std::min(g->sy, g->sz));
     c.guard = 1 + (int)std::floor(g->dt / smin);
     // slab planes start so that (first plane - guard) is a multiple of the x alignment
     c.slab0 = -1 - (((-1 - c.guard) % align) + align) % align;

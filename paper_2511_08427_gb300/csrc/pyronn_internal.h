@@ -1,6 +1,7 @@
 // Internal declarations shared by the host geometry code, the C ABI and the CUDA kernels.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -264,5 +265,15 @@ int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, v
 int launch_bp_transpose(const OpParams &p, const void *vol, void *sino, float *acc32, int dtype, void *stream);
 
 size_t dtype_size(int dtype);
+
+// Box extent (voxels) covering a span of index coordinates plus a margin, at most cap; -1 where the
+// span is not finite (a corner ray parallel to the slab planes), which bounds nothing: the kernels
+// test every tile's box against the buffer and send tiles that do not fit to global loads.
+inline long long box_extent(double span, long long pad, long long cap) {
+    if (!(span >= 0.0) || !std::isfinite(span)) return -1;
+    if (!(span < (double)cap)) return cap;
+    const long long e = (long long)std::ceil(span) + pad;
+    return e < cap ? e : cap;
+}
 
 }  // namespace pyronn

@@ -122,6 +122,39 @@ def test_invalid_arguments_are_rejected(L):
     assert b"null" in L.pyronn_last_error()
 
 
+def test_values_outside_the_device_tables_are_rejected(L):
+    """Non-finite offsets, spacings whose value or reciprocal is not finite in FP32, orbits whose
+    FP32 view tables would overflow, and steps that give more than 2^22 samples across the volume are
+    rejected at create / set time with INVALID_ARG; a step of 2^16 voxels or more is accepted and
+    routed to the generic projector and adjoint instead of the slab-staged ones."""
+    from paper_2511_08427_gb300.operators import Geometry
+    nan, inf = float("nan"), float("inf")
+    bad = [dict(volume_offset=(0.0, nan, 0.0)), dict(volume_offset=(inf, 0.0, 0.0)),
+           dict(detector_offset=(0.0, nan)), dict(volume_spacing=(1.0, 1e-300, 1.0)),
+           dict(volume_spacing=(1e300, 1.0, 1.0)), dict(detector_spacing=(1.0, 1e-60)),
+           dict(sid=1e300, sdd=2e300)]
+    for kw in bad:
+        args = dict(volume_shape=(8, 8, 8), volume_spacing=(1.0, 1.0, 1.0), detector_shape=(8, 8),
+                    detector_spacing=(1.0, 1.0), number_of_projections=3, angular_range=2 * math.pi,
+                    sid=100.0, sdd=200.0)
+        args.update(kw)
+        with pytest.raises(_lib.PyronnError) as e:
+            Geometry.cone_circular(**args)
+        assert e.value.code == -1, kw
+    g = Geometry.cone_circular((8, 16, 16), (1.0, 1.0, 1.0), (8, 8), (1.0, 1.0), 3, 2 * math.pi, 100.0, 200.0)
+    diag = math.sqrt(17 ** 2 + 17 ** 2 + 9 ** 2)           # support box (-1, N) on every axis, in mm
+    with pytest.raises(_lib.PyronnError) as e:
+        g.step = diag / 2 ** 22 * 0.99
+    assert e.value.code == -1 and b"2^22" in L.pyronn_last_error()
+    g.step = diag / 2 ** 22 * 1.01
+    assert g.count_samples() > 0
+    g.step = 0.5
+    assert g.fp_config()["kernel"] in (2, 3) and g.adjoint_config()["kernel"] == 3
+    g.step = 70000.0                                         # more than 2^16 voxels per sample
+    assert g.fp_config()["kernel"] == 1 and g.adjoint_config()["kernel"] == 2
+    assert g.count_samples() <= 3 * 8 * 8                    # at most one sample per ray
+
+
 def test_step_changes_sample_count(L):
     from paper_2511_08427_gb300.operators import Geometry
     g = Geometry.parallel2d((8, 20), (1.0, 1.0), 5, 1.0, 1)
