@@ -8,7 +8,7 @@ from __future__ import annotations
 import torch
 
 from ._lib import check, lib
-from .operators import Geometry, _batch, _check, _sino_dims, _stream_ptr
+from .operators import Geometry, _batch, _check, _check_like, _sino_dims, _stream_ptr
 
 
 def _prep(sino: torch.Tensor, g: Geometry):
@@ -48,6 +48,7 @@ def gaussian_noise(sino: torch.Tensor, g: Geometry, noise: torch.Tensor, mean: f
         raise ValueError("noise must have one sample per sinogram element")
     if out is None:
         out = torch.empty_like(sino)
+    _check_like(out, sino.shape, sino.dtype, sino.device, "out")
     with torch.cuda.device(sino.device):
         check(lib().pyronn_sim_gaussian_noise(g.handle, sino.data_ptr(), out.data_ptr(), nz.data_ptr(), float(mean),
                                               float(std), dt, nb, _stream_ptr(sino.device)))
@@ -64,6 +65,7 @@ def ring_artifacts(sino: torch.Tensor, g: Geometry, columns, gains, view_begin: 
         raise ValueError("one gain per column")
     if out is None:
         out = torch.empty_like(sino)
+    _check_like(out, sino.shape, sino.dtype, sino.device, "out")
     ve = g.n_views if view_end is None else int(view_end)
     with torch.cuda.device(sino.device):
         check(lib().pyronn_sim_ring(g.handle, sino.data_ptr(), out.data_ptr(), cols.data_ptr(), gs.data_ptr(),

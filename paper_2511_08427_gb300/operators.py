@@ -225,6 +225,20 @@ def _check(t: torch.Tensor, what: str) -> int:
     return _DTYPES[t.dtype]
 
 
+def _check_like(t: torch.Tensor, shape, dtype, device, what: str) -> torch.Tensor:
+    """A caller-supplied tensor the library writes (or reads in place) must match exactly: the library
+    sees only a pointer, so a wrong size, type, device or layout would let it run past the tensor."""
+    if t.device != device:
+        raise ValueError(f"{what} must be on {device}, got {t.device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t
+
+
 def _stream_ptr(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
@@ -236,6 +250,7 @@ def forward_project(vol: torch.Tensor, g: Geometry, out: torch.Tensor | None = N
     lead, nb = _batch(vol, _vol_dims(g), "volume")
     if out is None:
         out = torch.empty(lead + _sino_dims(g), dtype=vol.dtype, device=vol.device)
+    _check_like(out, lead + _sino_dims(g), vol.dtype, vol.device, "out")
     with torch.cuda.device(vol.device):
         check(lib().pyronn_fp(g.handle, vol.data_ptr(), out.data_ptr(), dt, nb, _stream_ptr(vol.device)))
     return out
@@ -248,6 +263,7 @@ def adjoint(sino: torch.Tensor, g: Geometry, out: torch.Tensor | None = None) ->
     lead, nb = _batch(sino, _sino_dims(g), "sinogram")
     if out is None:
         out = torch.empty(lead + _vol_dims(g), dtype=sino.dtype, device=sino.device)
+    _check_like(out, lead + _vol_dims(g), sino.dtype, sino.device, "out")
     with torch.cuda.device(sino.device):
         check(lib().pyronn_adjoint(g.handle, sino.data_ptr(), out.data_ptr(), dt, nb, _stream_ptr(sino.device)))
     return out
@@ -258,19 +274,12 @@ def adjoint_update(vol: torch.Tensor, sino: torch.Tensor, g: Geometry, alpha: fl
     """vol += alpha A^T (sino - sino_b) in place (sino_b optional): the fused data-term update of a
     gradient step (pyronn_adjoint_update). Returns vol."""
     dt = _check(sino, "sinogram")
-    if vol.dtype != sino.dtype or (sino_b is not None and sino_b.dtype != sino.dtype):
-        raise TypeError("volume and sinograms must share one element type")
-    if not vol.is_contiguous():
-        raise ValueError("the updated volume must be contiguous")
     sino = sino.contiguous()
     lead, nb = _batch(sino, _sino_dims(g), "sinogram")
-    if tuple(vol.shape) != lead + _vol_dims(g):
-        raise ValueError(f"volume shape {tuple(vol.shape)} does not match {lead + _vol_dims(g)}")
+    _check_like(vol, lead + _vol_dims(g), sino.dtype, sino.device, "the updated volume")
     sb = 0
     if sino_b is not None:
-        sino_b = sino_b.contiguous()
-        if sino_b.shape != sino.shape:
-            raise ValueError("sino_b must have the shape of sino")
+        sino_b = _check_like(sino_b.contiguous(), sino.shape, sino.dtype, sino.device, "sino_b")
         sb = sino_b.data_ptr()
     with torch.cuda.device(sino.device):
         check(lib().pyronn_adjoint_update(g.handle, sino.data_ptr(), sb, float(alpha), vol.data_ptr(), dt, nb,
@@ -291,6 +300,7 @@ def fbp_filter(sino: torch.Tensor, g: Geometry, filter: int = FILTER_RAM_LAK,
     lead, nb = _batch(sino, _sino_dims(g), "sinogram")
     if out is None:
         out = torch.empty_like(sino)
+    _check_like(out, sino.shape, sino.dtype, sino.device, "out")
     with torch.cuda.device(sino.device):
         check(lib().pyronn_fbp_filter(g.handle, sino.data_ptr(), out.data_ptr(), int(filter), dt, nb,
                                       _stream_ptr(sino.device)))
@@ -310,6 +320,7 @@ def back_project(sino: torch.Tensor, g: Geometry, weight: int = BP_PLAIN, out: t
     lead, nb = _batch(sino, _sino_dims(g), "sinogram")
     if out is None:
         out = torch.empty(lead + _vol_dims(g), dtype=sino.dtype, device=sino.device)
+    _check_like(out, lead + _vol_dims(g), sino.dtype, sino.device, "out")
     with torch.cuda.device(sino.device):
         check(lib().pyronn_bp(g.handle, sino.data_ptr(), out.data_ptr(), dt, nb, int(weight),
                               _stream_ptr(sino.device)))
@@ -324,6 +335,7 @@ def back_project_transpose(vol: torch.Tensor, g: Geometry, weight: int = BP_PLAI
     lead, nb = _batch(vol, _vol_dims(g), "volume")
     if out is None:
         out = torch.empty(lead + _sino_dims(g), dtype=vol.dtype, device=vol.device)
+    _check_like(out, lead + _sino_dims(g), vol.dtype, vol.device, "out")
     with torch.cuda.device(vol.device):
         check(lib().pyronn_bp_transpose(g.handle, vol.data_ptr(), out.data_ptr(), dt, nb, int(weight),
                                         _stream_ptr(vol.device)))
@@ -366,6 +378,8 @@ class Plan:
             if t.dtype != self.dtype or tuple(t.shape) != tuple(shp) or not t.is_contiguous():
                 raise ValueError(f"{what}: expected contiguous {self.dtype} of shape {tuple(shp)}, got "
                                  f"{t.dtype} {tuple(t.shape)}")
+            if t.device != tensors[0].device:
+                raise ValueError(f"{what}: all tensors of a plan call must be on one device")
         return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
 
     def forward_project(self, vols, sinos):

@@ -234,3 +234,27 @@ def test_argument_checks_precede_the_device(L):
     assert L.pyronn_sim_ring(h, a, b, a, a, 1, 2, 9, 0, 1, None) == -1    # views [2, 9) of 3
     assert L.pyronn_sim_gaussian_noise(h, a, b, None, 0.0, 1.0, 0, 1, None) == -1
     assert L.pyronn_fp(h, ctypes.c_void_p(8), b, 0, 1, None) == -3        # misaligned
+
+
+def test_caller_tensors_are_checked_before_the_library_sees_them(L):
+    """The library sees only pointers, so the binding checks every tensor it hands over: inputs must be
+    CUDA tensors of a supported type, and caller-supplied outputs or in-place operands must match the
+    expected shape, type and device and be contiguous. These checks run before any device work."""
+    import torch
+    from paper_2511_08427_gb300 import operators as ops
+    g = ops.Geometry.cone_circular((4, 6, 8), (1.0, 1.0, 1.0), (5, 7), (1.0, 1.0), 3, 2 * math.pi, 50.0, 90.0)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        ops.forward_project(torch.zeros(4, 6, 8), g)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        ops.adjoint_update(torch.zeros(4, 6, 8), torch.zeros(3, 5, 7), g, 0.5)
+    cpu = torch.device("cpu")
+    good = torch.zeros(2, 3, 5, 7)
+    assert ops._check_like(good, (2, 3, 5, 7), torch.float32, cpu, "out") is good
+    with pytest.raises(ValueError, match="shape"):
+        ops._check_like(torch.zeros(2, 3, 5, 6), (2, 3, 5, 7), torch.float32, cpu, "out")
+    with pytest.raises(TypeError):
+        ops._check_like(good.to(torch.bfloat16), (2, 3, 5, 7), torch.float32, cpu, "out")
+    with pytest.raises(ValueError, match="contiguous"):
+        ops._check_like(torch.zeros(2, 3, 7, 5).transpose(-1, -2), (2, 3, 5, 7), torch.float32, cpu, "out")
+    with pytest.raises(ValueError, match="must be on"):
+        ops._check_like(good, (2, 3, 5, 7), torch.float32, torch.device("cuda", 0), "out")
