@@ -194,6 +194,57 @@ def test_fp_config_invariants(L, dtype_size, dtype):
     assert g2.fp_config(td)["kernel"] == 1
 
 
+def test_config_invariants_over_random_geometries(L):
+    """The TMA alignment and shared-memory budgets hold for every geometry, not only the hand-picked
+    ones: 120 seeded random cone geometries (sizes, anisotropic spacings, offsets, helices, detector
+    sizes, steps), each storage type and both x-march staging choices. Wherever the TMA projector is
+    chosen, x-march boxes start and stay 16-byte aligned along their innermost axis and fit 200 KB;
+    wherever the slab adjoint is chosen, its box (at most 160 KB) and slab table fit 200 KB."""
+    import random
+    import torch
+    from paper_2511_08427_gb300.operators import TUNE_FP_TRANSPOSE, Geometry
+    rnd = random.Random(2024)
+    seen_tma = seen_adj = 0
+    for _ in range(120):
+        shape = tuple(rnd.choice([8, 12, 16, 24, 32, 40, 48, 64, 96]) for _ in range(3))
+        sp = tuple(rnd.choice([0.25, 0.4, 0.5, 0.8, 1.0, 2.0]) for _ in range(3))
+        det = (rnd.choice([8, 16, 24, 40, 64]), rnd.choice([8, 16, 33, 64, 100]))
+        dsp = (rnd.choice([0.3, 0.6, 1.2]), rnd.choice([0.3, 0.6, 1.2, 3.0]))
+        sid = rnd.choice([20.0, 60.0, 150.0, 750.0])
+        g = Geometry.cone_circular(shape, sp, det, dsp, rnd.choice([1, 5, 12]), 2 * math.pi, sid,
+                                   sid * rnd.choice([1.3, 1.6, 2.5]), helical_pitch=rnd.choice([0.0, 0.0, 6.0]),
+                                   volume_offset=tuple(rnd.choice([0.0, 2.5, -4.0]) for _ in range(3)))
+        if rnd.random() < 0.5:
+            g.step = min(sp) * rnd.choice([0.25, 0.5, 1.0, 2.5])
+        for td, size in ((torch.float32, 4), (torch.bfloat16, 2), (torch.float16, 2)):
+            align = 16 // size
+            for transpose in (0, 1):
+                g.set_tuning(TUNE_FP_TRANSPOSE, transpose)
+                c = g.fp_config(td)
+                if c["kernel"] != 3:
+                    assert (shape[2] * size) % 16 != 0 or c["kernel"] in (1, 2)
+                    continue
+                seen_tma += 1
+                assert (shape[2] * size) % 16 == 0
+                assert c["depth"] % align == 0 and (c["slab0"] - c["guard"]) % align == 0
+                assert c["slab0"] - c["guard"] <= -1 - c["guard"]
+                assert c["y_fastest_x_march"] == (transpose == 0 and (shape[1] * size) % 16 == 0)
+                for m, box in enumerate(c["box"]):
+                    assert all(1 <= e <= 256 for e in box), box
+                    inner = 1 if (m == 0 and c["y_fastest_x_march"]) else 0
+                    assert (box[inner] * size) % 16 == 0, (m, box)
+                assert c["smem_bytes"] <= 200 * 1024 + 128
+        a = g.adjoint_config()
+        if a["kernel"] == 3:
+            seen_adj += 1
+            assert a["depth"] in (8, 6, 5, 4) and a["guard"] >= 1
+            assert a["max_slabs"] == (max(shape) + 2 + a["depth"] - 1) // a["depth"]
+            # the box itself at most 160 KB; box and slab table within the 200 KB the kernel is given
+            assert a["box_floats"] <= 40 * 1024
+            assert 4 * ((a["box_floats"] + 3) // 4 * 4) + 104 * a["max_slabs"] <= 200 * 1024
+    assert seen_tma > 100 and seen_adj > 60
+
+
 def test_adjoint_config_invariants(L):
     """Slab adjoint: the slab table holds every slab of the longest axis at the chosen depth; box and
     table fit the two-CTAs-per-SM budget (112 KB each); the odd x-march pitch is on by default and the
