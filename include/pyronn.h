@@ -135,6 +135,9 @@ PYRONN_API int pyronn_geom_create_cone_matrices(const pyronn_vol_desc *vol, cons
 PYRONN_API int pyronn_geom_create_matrices2d(const pyronn_vol_desc *vol, const pyronn_det_desc *det, int n_views,
                                   const double *P, pyronn_geom_t *out);
 
+/* Releases the handle with its host tables and every device buffer, stream and event it owns (on the
+ * device they were created on). NULL is accepted and does nothing. The caller must make sure no
+ * operation that uses g is still running on any stream (synchronise first); g is invalid afterwards. */
 PYRONN_API int pyronn_geom_destroy(pyronn_geom_t g);
 
 /* Sampling step along rays in mm (> 0). Default: half the smallest voxel spacing. PYRONN_INVALID_ARG
@@ -142,9 +145,11 @@ PYRONN_API int pyronn_geom_destroy(pyronn_geom_t g);
  * ((-1, N) voxels on every axis) spans more than 2^22 steps. Steps of 2^16 voxels or more are accepted
  * and run on the direct projector and the brick adjoint (the slab-staged kernels need fewer). */
 PYRONN_API int pyronn_geom_set_step(pyronn_geom_t g, double dt_mm);
+/* The current step in mm, written to *dt_mm (PYRONN_INVALID_ARG for a NULL argument). */
 PYRONN_API int pyronn_geom_get_step(pyronn_geom_t g, double *dt_mm);
 
-/* Number of views; geometry kind (0 parallel, 1 perspective). */
+/* Number of views, geometry kind (0 parallel, 1 perspective) and dimension (2 or 3); any output
+ * pointer may be NULL. */
 PYRONN_API int pyronn_geom_info(pyronn_geom_t g, int *n_views, int *kind, int *ndim);
 
 /* Copy out the normalised per-view matrices: n_views x 12 doubles. Perspective views: P (3 x 4).
