@@ -35,6 +35,15 @@
  * the legacy default stream) and never synchronise, except the *_host variants.
  * The first operator call of a geometry on a device uploads its per-view tables with a
  * synchronous copy; make that call before capturing a CUDA graph.
+ *
+ * Threads and streams: calls on different geometries are independent. Calls on one geometry may
+ * come from several host threads (its lazily built tables, configurations and sample count are
+ * set up under a lock), but on the device they must be ordered, on one stream or with events:
+ * several operators use geometry-owned work buffers (the forward projector's y-fastest volume
+ * copy, the FP32 accumulation of BF16 / FP16 adjoints, the update and host staging buffers). For
+ * concurrent work use one geometry per stream, or a plan. The setters (pyronn_geom_set_step,
+ * _set_variant, _set_tuning) and pyronn_geom_destroy must not run while another call uses the
+ * same geometry.
  */
 #ifndef PYRONN_H
 #define PYRONN_H

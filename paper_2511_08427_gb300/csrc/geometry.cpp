@@ -647,9 +647,12 @@ int pyronn_geom_get_views(pyronn_geom_t g, double *out) {
 int pyronn_geom_count_samples(pyronn_geom_t g, int64_t *total) {
     clear_error();
     if (!g || !total) return set_error(PYRONN_INVALID_ARG, "null argument");
-    if (g->sample_count >= 0) {
-        *total = g->sample_count;
-        return PYRONN_OK;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (g->sample_count >= 0) {
+            *total = g->sample_count;
+            return PYRONN_OK;
+        }
     }
     // FP64 ray setup from the FP64 views (same construction as the device tables, unrounded)
     const int V = g->n_views;
@@ -727,8 +730,12 @@ int pyronn_geom_count_samples(pyronn_geom_t g, int64_t *total) {
     for (unsigned i = 1; i < nt; ++i) th.emplace_back(work);
     work();
     for (auto &t : th) t.join();
-    g->sample_count = sum.load();
-    *total = g->sample_count;
+    const long long count = sum.load();
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        g->sample_count = count;
+    }
+    *total = count;
     return PYRONN_OK;
 }
 

@@ -309,3 +309,35 @@ def test_caller_tensors_are_checked_before_the_library_sees_them(L):
         ops._check_like(torch.zeros(2, 3, 7, 5).transpose(-1, -2), (2, 3, 5, 7), torch.float32, cpu, "out")
     with pytest.raises(ValueError, match="must be on"):
         ops._check_like(good, (2, 3, 5, 7), torch.float32, torch.device("cuda", 0), "out")
+
+
+def test_concurrent_queries_on_one_geometry_agree(L):
+    """Eight host threads query one fresh geometry at once (ctypes releases the interpreter lock, so
+    the library calls overlap): the lazily built configurations and the cached sample count are set
+    up under the geometry's lock, and every thread sees the serial results."""
+    import threading
+    import torch
+    from paper_2511_08427_gb300.operators import Geometry
+    args = ((24, 32, 40), (0.5, 0.5, 0.5), (20, 28), (0.8, 0.8), 16, 2 * math.pi, 100.0, 160.0)
+    ref = Geometry.cone_circular(*args)
+    want = (ref.count_samples(), ref.fp_config(torch.float32), ref.fp_config(torch.bfloat16), ref.adjoint_config())
+    for _ in range(3):
+        g = Geometry.cone_circular(*args)
+        got, errs = [], []
+        start = threading.Barrier(8)
+
+        def work():
+            try:
+                start.wait()
+                got.append((g.count_samples(), g.fp_config(torch.float32), g.fp_config(torch.bfloat16),
+                            g.adjoint_config()))
+            except Exception as e:      # surfaced below
+                errs.append(e)
+
+        th = [threading.Thread(target=work) for _ in range(8)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert not errs and len(got) == 8
+        assert all(r == want for r in got)
