@@ -341,3 +341,25 @@ def test_concurrent_queries_on_one_geometry_agree(L):
             t.join()
         assert not errs and len(got) == 8
         assert all(r == want for r in got)
+
+
+def test_plan_arguments_are_checked_before_the_device(L):
+    """Batched plans: the geometry count (1 to 16), null arrays and handles and the element type are
+    checked before any device work; plan operators reject a null plan."""
+    from paper_2511_08427_gb300.operators import Geometry
+    g = Geometry.cone_circular((8, 8, 8), (1.0, 1.0, 1.0), (8, 8), (1.0, 1.0), 4, 2 * math.pi, 50.0, 90.0)
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 17)(*([g.handle.value] * 17))
+    assert L.pyronn_plan_create(0, arr, 0, ctypes.byref(h)) == -1
+    assert L.pyronn_plan_create(17, arr, 0, ctypes.byref(h)) == -1 and b"1 to 16" in L.pyronn_last_error()
+    assert L.pyronn_plan_create(2, None, 0, ctypes.byref(h)) == -1
+    assert L.pyronn_plan_create(2, arr, 0, None) == -1
+    assert L.pyronn_plan_create(2, arr, 7, ctypes.byref(h)) == -2
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert L.pyronn_plan_create(2, nulls, 0, ctypes.byref(h)) == -1 and b"null" in L.pyronn_last_error()
+    assert not h.value
+    ptrs = (ctypes.c_void_p * 1)(16)
+    assert L.pyronn_plan_fp(None, ptrs, ptrs, None) == -1
+    assert L.pyronn_plan_adjoint(None, ptrs, ptrs, None) == -1
+    assert L.pyronn_plan_bp(None, ptrs, ptrs, 0, None) == -1
+    assert L.pyronn_plan_destroy(None) == 0
