@@ -363,3 +363,18 @@ def test_plan_arguments_are_checked_before_the_device(L):
     assert L.pyronn_plan_adjoint(None, ptrs, ptrs, None) == -1
     assert L.pyronn_plan_bp(None, ptrs, ptrs, 0, None) == -1
     assert L.pyronn_plan_destroy(None) == 0
+
+
+def test_size_limits_at_their_edges(L):
+    """Volume sides up to 16384, detector sides up to 65536 and up to 2^20 views are accepted; one more
+    is rejected before anything is allocated. The largest accepted volume and detector are created
+    (host tables only) and report their shapes."""
+    from paper_2511_08427_gb300.operators import Geometry
+    g = Geometry.parallel2d((16384, 16384), (0.1, 0.1), 65536, 0.05, 2)
+    assert g.volume_shape == (16384, 16384) and g.sinogram_shape == (2, 65536)
+    for kw in (dict(shape=(16385, 8)), dict(nb=65537), dict(views=(1 << 20) + 1), dict(views=0), dict(nb=0)):
+        with pytest.raises(_lib.PyronnError) as e:
+            Geometry.parallel2d(kw.get("shape", (8, 8)), (1.0, 1.0), kw.get("nb", 8), 1.0, kw.get("views", 4))
+        assert e.value.code == -1, kw
+    with pytest.raises(_lib.PyronnError):
+        Geometry.cone_circular((16385, 4, 4), (1.0, 1.0, 1.0), (4, 4), (1.0, 1.0), 2, 1.0, 50.0, 90.0)
