@@ -42,6 +42,8 @@ MUTANTS = [
      [("test_axis_aligned_3d_rays_trilinear",)]),
     ("support box drops the first x slab", "return q[0] > -1.0 && q[0] < g->nx", "return q[0] > 0.0 && q[0] < g->nx",
      [("test_axis_aligned_rays_are_exact_discrete_line_sums",)]),
+    ("support box clipped at the voxel edges along y", "q[1] > -1.0 && q[1] < g->ny",
+     "q[1] > -0.5 && q[1] < g->ny - 0.5", [("test_fp_is_continuous_in_the_geometry",)]),
     ("ray direction with u and v swapped",
      "d[i] = Mi[3 * i + 0] * u + Mi[3 * i + 1] * v + Mi[3 * i + 2];",
      "d[i] = Mi[3 * i + 0] * v + Mi[3 * i + 1] * u + Mi[3 * i + 2];", [("test_brute_force_system_matrix", "cone")]),

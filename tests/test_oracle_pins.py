@@ -334,6 +334,31 @@ def test_volume_offset_is_a_world_translation(oracle_lib):
     assert rel_l2(o.bp(h1, q2), o.bp(h0, q2)) < 1e-12
 
 
+def test_fp_is_continuous_in_the_geometry(oracle_lib):
+    """Sample weights vanish on the boundary of the open support box and the hat basis is continuous,
+    so the forward projection is a continuous function of the geometry: rays lying exactly on a row
+    boundary, through row centres, or on the support's edge (index -1 and N) agree with rays shifted a
+    nanometre either way, to first order in the shift (parallel beam at t = 0, rays along -x)."""
+    o = oracle_lib
+    ny, nx = 7, 9
+    f = np.random.default_rng(9).random((ny, nx)) + 0.5
+    # bin u = 0 of a one-bin detector sits at y = ou; row j's centre is y = j - (ny - 1) / 2
+    for yq in (-1.0, -0.5, 0.0, 0.5, 2.0, 3.5, 6.0, 7.0):
+        y0 = yq - (ny - 1) / 2                      # index coordinate yq -> world y
+        vals = []
+        for eps in (-1e-9, 0.0, 1e-9):
+            g = o.parallel2d((ny, nx), (1.0, 1.0), 1, 1.0, 1, math.pi, det_offset=y0 + eps, dt=0.25)
+            vals.append(o.fp(g, f)[0, 0, 0])
+        assert abs(vals[1] - vals[0]) < 1e-7 and abs(vals[2] - vals[1]) < 1e-7, (yq, vals)
+        if yq in (-1.0, 7.0):                       # the support's edge: the line sum is zero there
+            assert abs(vals[1]) < 1e-12
+    # oblique cone rays: a small change of the source distance moves the projection a little
+    g1 = o.cone_circular((6, 7, 8), (1.0, 1.0, 1.0), (9, 11), (1.0, 1.0), 3, 2 * math.pi, 40.0, 70.0)
+    g2 = o.cone_circular((6, 7, 8), (1.0, 1.0, 1.0), (9, 11), (1.0, 1.0), 3, 2 * math.pi, 40.0 + 1e-9, 70.0)
+    x = np.random.default_rng(10).random((6, 7, 8))
+    assert np.max(np.abs(o.fp(g1, x) - o.fp(g2, x))) < 1e-6
+
+
 def test_fp_converges_to_ellipse_chords(oracle_lib):
     """2D parallel beam, 10 random ellipses: rel-L2 to the analytic chord sums is small at 128^2
     and shrinks when the grid is refined (orientation or offset mistakes give O(1) errors)."""
