@@ -44,6 +44,15 @@ MUTANTS = [
      [("test_axis_aligned_rays_are_exact_discrete_line_sums",)]),
     ("support box clipped at the voxel edges along y", "q[1] > -1.0 && q[1] < g->ny",
      "q[1] > -0.5 && q[1] < g->ny - 0.5", [("test_fp_is_continuous_in_the_geometry",)]),
+    ("FP interpolation clamps to the edge instead of zero padding",
+     "                if (i < 0 || i >= g->nx || j < 0 || j >= g->ny || k < 0 || k >= g->nz) continue;\n"
+     "                double w = hat(q[0] - i) * hat(q[1] - j) * hat(q[2] - k);\n"
+     "                s += w * vol[((size_t)k * g->ny + j) * g->nx + i];",
+     "                double w = hat(q[0] - i) * hat(q[1] - j) * hat(q[2] - k);\n"
+     "                long ic = i < 0 ? 0 : (i >= g->nx ? g->nx - 1 : i), jc = j < 0 ? 0 : (j >= g->ny ? g->ny - 1 : j);\n"
+     "                long kc = k < 0 ? 0 : (k >= g->nz ? g->nz - 1 : k);\n"
+     "                s += w * vol[((size_t)kc * g->ny + jc) * g->nx + ic];",
+     [("test_axis_aligned_rays_are_exact_discrete_line_sums",), ("test_fp_is_continuous_in_the_geometry",)]),
     ("ray direction with u and v swapped",
      "d[i] = Mi[3 * i + 0] * u + Mi[3 * i + 1] * v + Mi[3 * i + 2];",
      "d[i] = Mi[3 * i + 0] * v + Mi[3 * i + 1] * u + Mi[3 * i + 2];", [("test_brute_force_system_matrix", "cone")]),
@@ -75,6 +84,12 @@ MUTANTS = [
      [("test_bp_voxels_behind_the_source_receive_nothing",)]),
     ("parallel BP detector offset with the wrong sign", "- g->ou) / g->du + 0.5 * (g->nu - 1);",
      "+ g->ou) / g->du + 0.5 * (g->nu - 1);", [("test_parallel_bp_detector_offset",)]),
+    ("BP detector taps clamp to the edge instead of zero padding",
+     "                if (uu < 0 || uu >= g->nu || vv < 0 || vv >= g->nv) continue;\n"
+     "                s += q[(size_t)vv * g->nu + uu] * hat(u - uu) * hat(v - vv);",
+     "                long uc = uu < 0 ? 0 : (uu >= g->nu ? g->nu - 1 : uu), vc = vv < 0 ? 0 : (vv >= g->nv ? g->nv - 1 : vv);\n"
+     "                s += q[(size_t)vc * g->nu + uc] * hat(u - uu) * hat(v - vv);",
+     [("test_bp_voxels_behind_the_source_receive_nothing",), ("test_parallel_bp_detector_offset",)]),
     # geometry (Sec. 2.4)
     ("pixel (0, 0) half a pixel off along u", "D0[i] = Dc[i] + (ou - 0.5 * (nu - 1) * du) * a[i]",
      "D0[i] = Dc[i] + (ou - 0.5 * nu * du) * a[i]", [("test_listing1_geometry_pins",)]),
