@@ -223,8 +223,8 @@ def jittered_circular_trajectory(n_views: int, angular_range: float, sid: float,
 def batched_cone_workload(n_volumes: int = 16, voxel_mm: float = 0.5, sid: float = 750.0, sdd: float = 1200.0):
     """Parameters of the uneven batched cone-beam workload (16 volumes, 96^3 ... 256^3).
 
-    Volume i: cube side 8 * round((96 + i * 160 / 15) / 8) (uneven sizes; rows a multiple of 32
-    bytes so that BF16 tensor copies apply), views 180 + round(i * 360 / 15),
+    Volume i: cube side 8 * round((96 + i * 160 / 15) / 8) (uneven sizes; rows a multiple of 16
+    bytes even in BF16, so that tensor copies apply to every storage type), views 180 + round(i * 360 / 15),
     detector side 256 + 16 * round(i * 16 / 15); circular orbit for even i, one-turn helix for
     odd i with pitch = half the detector height at the isocentre. The pixel size is chosen so
     that the volume's xy diagonal, magnified by sdd / sid, fills 90 % of the detector width.
