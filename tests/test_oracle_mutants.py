@@ -64,6 +64,9 @@ MUTANTS = [
      "double C[3] = {0.0, 0.0, 0.0};", [("test_volume_offset_is_a_world_translation",)]),
     ("sample index adds the volume offset", "q[0] = (X[0] - g->ox) / g->sx", "q[0] = (X[0] + g->ox) / g->sx",
      [("test_volume_offset_is_a_world_translation",)]),
+    ("sampled rays read one ray further", "for (long i = 0; i < n; ++i) out[i] = fp_one(g, vol, (long)ids[i]);",
+     "for (long i = 0; i < n; ++i) out[i] = fp_one(g, vol, (long)ids[i] + 1);",
+     [("test_fp_rays_and_bp_voxels_subsets_match_full",)]),
     # matched adjoint (Sec. 2.2)
     ("adjoint without dt", "vol[((size_t)kk * g->ny + j) * g->nx + i] += y * g->dt * w;",
      "vol[((size_t)kk * g->ny + j) * g->nx + i] += y * w;", [("test_dot_product_adjoint", "parallel")]),
@@ -90,6 +93,10 @@ MUTANTS = [
      "                long uc = uu < 0 ? 0 : (uu >= g->nu ? g->nu - 1 : uu), vc = vv < 0 ? 0 : (vv >= g->nv ? g->nv - 1 : vv);\n"
      "                s += q[(size_t)vc * g->nu + uc] * hat(u - uu) * hat(v - vv);",
      [("test_bp_voxels_behind_the_source_receive_nothing",), ("test_parallel_bp_detector_offset",)]),
+    ("sampled voxels read one voxel further",
+     "for (long i = 0; i < n; ++i) out[i] = bp_one(g, sino, weight_mode, (long)ids[i]);",
+     "for (long i = 0; i < n; ++i) out[i] = bp_one(g, sino, weight_mode, (long)ids[i] + 1);",
+     [("test_fp_rays_and_bp_voxels_subsets_match_full",)]),
     # geometry (Sec. 2.4)
     ("pixel (0, 0) half a pixel off along u", "D0[i] = Dc[i] + (ou - 0.5 * (nu - 1) * du) * a[i]",
      "D0[i] = Dc[i] + (ou - 0.5 * nu * du) * a[i]", [("test_listing1_geometry_pins",)]),

@@ -467,6 +467,22 @@ def test_adjoint_rays_subset_matches_full(oracle_lib):
     assert np.allclose(o.adjoint(g, y), o.adjoint_rays(g, ids, y.ravel()[ids]), atol=1e-13)
 
 
+def test_fp_rays_and_bp_voxels_subsets_match_full(oracle_lib):
+    """The sampled entry points used for full-size parity address rays as (view * Nv + v) * Nu + u and
+    voxels as (k * Ny + j) * Nx + i, and return exactly the full operators' values there."""
+    o = oracle_lib
+    rng = np.random.default_rng(12)
+    g = o.cone_circular((7, 9, 10), (1.0, 0.8, 1.1), (8, 11), (1.2, 1.0), 5, 2 * math.pi, 60.0, 100.0)
+    x = rng.random(g.vol_shape)
+    full = o.fp(g, x)
+    ids = np.unique(rng.integers(0, full.size - 1, 60))      # below the last, so a planted "+ 1" stays in range
+    assert np.array_equal(o.fp_rays(g, x, ids), full.ravel()[ids])
+    q = rng.random(g.sino_shape)
+    vids = np.unique(rng.integers(0, x.size - 1, 60))
+    for w in (0, 1):
+        assert np.array_equal(o.bp_voxels(g, q, vids, w), o.bp(g, q, w).ravel()[vids])
+
+
 # ------------------------------------------------------------------------------------------------
 # voxel-driven back-projection pins (Sec. 2.1)
 # ------------------------------------------------------------------------------------------------
