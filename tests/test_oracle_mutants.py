@@ -67,6 +67,14 @@ MUTANTS = [
     ("sampled rays read one ray further", "for (long i = 0; i < n; ++i) out[i] = fp_one(g, vol, (long)ids[i]);",
      "for (long i = 0; i < n; ++i) out[i] = fp_one(g, vol, (long)ids[i] + 1);",
      [("test_fp_rays_and_bp_voxels_subsets_match_full",)]),
+    ("sample count includes samples outside the support box", "total += in_box(g, q);", "total += 1;",
+     [("test_constant_volume_axis_ray_and_sample_count",)]),
+    ("parallel ray origin with the u offset subtracted",
+     "double su = (u - 0.5 * (g->nu - 1)) * g->du + g->ou;", "double su = (u - 0.5 * (g->nu - 1)) * g->du - g->ou;",
+     [("test_axis_aligned_rays_are_exact_discrete_line_sums",)]),
+    ("parallel ray origin with the v spacing of u",
+     "double sv = (v - 0.5 * (g->nv - 1)) * g->dv + g->ov;", "double sv = (v - 0.5 * (g->nv - 1)) * g->du + g->ov;",
+     [("test_axis_aligned_3d_rays_trilinear",)]),
     # matched adjoint (Sec. 2.2)
     ("adjoint without dt", "vol[((size_t)kk * g->ny + j) * g->nx + i] += y * g->dt * w;",
      "vol[((size_t)kk * g->ny + j) * g->nx + i] += y * w;", [("test_dot_product_adjoint", "parallel")]),
