@@ -417,3 +417,47 @@ def test_sample_count_matches_oracle_over_random_geometries(L):
         g.step = dt
         og.dt = dt
         assert g.count_samples() == int(oracle.count_samples(og).sum()), (it, kind)
+
+
+def test_views_match_oracle_over_random_geometries(L):
+    """The library's normalised per-view matrices (FP64) equal the oracle's over seeded random
+    geometries: circular and helical cones with volume and detector offsets, jittered source /
+    detector positions, user matrices under random non-zero rescaling, fans and parallel beams."""
+    import random
+    from paper_2511_08427_gb300.operators import Geometry
+    rnd = random.Random(91)
+    for it in range(30):
+        shape = tuple(rnd.choice([6, 9, 12]) for _ in range(3))
+        sp = tuple(rnd.choice([0.4, 0.7, 1.0]) for _ in range(3))
+        det, dsp = (rnd.choice([5, 8]), rnd.choice([7, 12])), (rnd.choice([0.6, 1.1]), rnd.choice([0.5, 0.9]))
+        doff = (rnd.choice([0.0, 0.35]), rnd.choice([0.0, -0.6]))
+        off = tuple(rnd.choice([0.0, 2.0, -1.0]) for _ in range(3))
+        V, sid = rnd.choice([3, 6]), rnd.choice([40.0, 200.0])
+        sdd = sid * rnd.choice([1.5, 1.9])
+        k = it % 5
+        if k == 0:
+            pitch = rnd.choice([0.0, 3.0])
+            g = Geometry.cone_circular(shape, sp, det, dsp, V, 2 * math.pi, sid, sdd, helical_pitch=pitch,
+                                       volume_offset=off, detector_offset=doff)
+            og = oracle.cone_circular(shape, sp, det, dsp, V, 2 * math.pi, sid, sdd, pitch=pitch, vol_offset=off,
+                                      det_offset=doff)
+        elif k == 1:
+            tr = inputs.jittered_circular_trajectory(V, 2 * math.pi, sid, sdd, 0.5, 0.3, seed=it)
+            g = Geometry.cone_from_positions(shape, sp, det, dsp, tr.src, tr.det_centre, tr.eu, tr.ev,
+                                             volume_offset=off, detector_offset=doff)
+            og = oracle.cone_from_positions(shape, sp, det, dsp, tr.src, tr.det_centre, tr.eu, tr.ev, vol_offset=off,
+                                            det_offset=doff)
+        elif k == 2:
+            og0 = oracle.cone_circular(shape, sp, det, dsp, V, 2 * math.pi, sid, sdd, vol_offset=off)
+            scale = np.array([rnd.choice([-3.0, -0.2, 0.5, 7.0]) for _ in range(V)])
+            g = Geometry.cone_from_matrices(shape, sp, det, dsp, og0.views * scale[:, None], volume_offset=off)
+            og = og0
+        elif k == 3:
+            g = Geometry.fan2d(shape[1:], sp[1:], det[1], dsp[1], V, 2 * math.pi, sid, sdd)
+            og = oracle.fan_circular(shape[1:], sp[1:], det[1], dsp[1], V, 2 * math.pi, sid, sdd)
+        else:
+            g = Geometry.parallel2d(shape[1:], sp[1:], det[1], dsp[1], V, math.pi, detector_offset=doff[1])
+            og = oracle.parallel2d(shape[1:], sp[1:], det[1], dsp[1], V, math.pi, det_offset=doff[1])
+        assert g.kind == og.kind, it
+        assert np.allclose(g.views(), og.views, rtol=1e-12, atol=1e-12), it
+        assert abs(g.step - og.dt) < 1e-15, it
