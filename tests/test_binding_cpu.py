@@ -131,3 +131,33 @@ def test_plan_and_artifacts_marshal_lists(rec):
     name, a = rec.calls[-1]
     assert name == "pyronn_sim_ring" and a[1] == s.data_ptr() and a[2] == out.data_ptr() and a[5:8] == (2, 0, 2)
     plan._h = ctypes.c_void_p()     # the recorder created no plan
+
+
+def test_remaining_call_patterns(rec):
+    """The other patterns the GPU tests use: artifact calls (noise written in place), valid plan adjoint and
+    back-projection calls, and the unrolled reconstruction (checkpointed, fused and unfused) forward and
+    backward."""
+    from paper_2511_08427_gb300.unrolled import UnrolledGD
+    g = _cone()
+    s = torch.rand(2, 3, 5, 7)
+    j = artifacts.detector_jitter(s, g, torch.zeros(2, 3, 5, dtype=torch.int32), 0)
+    assert j.shape == s.shape and rec.calls[-1][0] == "pyronn_sim_detector_jitter" and rec.calls[-1][1][6] == 2
+    n = artifacts.gaussian_noise(s, g, torch.zeros_like(s), 0.1, 0.05, out=s)
+    assert n is s and rec.calls[-1][1][1] == rec.calls[-1][1][2] == s.data_ptr()
+    b = artifacts.motion_blur(s, g, [0.1, 0.2, 0.3], 3)
+    assert b.shape == s.shape and rec.calls[-1][0] == "pyronn_sim_motion_blur"
+    g2 = ops.Geometry.cone_circular((8, 8, 8), (1.0,) * 3, (6, 6), (1.0, 1.0), 2, 2 * math.pi, 40.0, 80.0)
+    plan = ops.Plan([g, g2])
+    sinos = [torch.rand(3, 5, 7), torch.rand(2, 6, 6)]
+    vols = [torch.empty(4, 6, 8), torch.empty(8, 8, 8)]
+    assert plan.adjoint(sinos, vols) is vols and rec.calls[-1][0] == "pyronn_plan_adjoint"
+    assert plan.back_project(sinos, vols, ops.BP_INV_W2) is vols and rec.calls[-1][1][3] == ops.BP_INV_W2
+    plan._h = ctypes.c_void_p()
+    cpu = torch.device("cpu")
+    for fused in (True, False):
+        net = UnrolledGD(g, iterations=3, alpha0=0.1, checkpoint=True, device=cpu, fused=fused)
+        p = torch.zeros(3, 5, 7)
+        x = net(p)
+        assert x.shape == (4, 6, 8)
+        x.sum().backward()
+        assert net.alpha.grad.shape == (3,)
