@@ -499,11 +499,15 @@ def test_many_views_times_batch_splits_launches(ops):
 
 def test_many_views_times_batch_splits_tma_launches(ops):
     """3D: V * B above the 65535 grid rows, so the TMA projector's launcher splits the batch (21 + 4
-    volumes) and makes the y-fastest copies per part; every volume equals its single projection, and the
-    slab adjoint's split batch matches its single calls."""
+    volumes) and makes the y-fastest copies per part; every volume equals its single projection. The
+    slab adjoint's split batch and its single calls each match the oracle at the FP32 parity bound:
+    they are not compared with each other bit for bit, because the boxes reach the volume through
+    FP32 global reductions whose order depends on scheduling (each result carries its own rounding,
+    about 1e-6 relative on a Gaussian cotangent over 3000 views)."""
     from paper_2511_08427_gb300.operators import Geometry
     V, B = 3000, 25
     g = Geometry.cone_circular((8, 8, 8), (1.0, 1.0, 1.0), (4, 4), (1.0, 1.0), V, 2 * math.pi, 30.0, 50.0)
+    og = oracle.cone_circular((8, 8, 8), (1.0, 1.0, 1.0), (4, 4), (1.0, 1.0), V, 2 * math.pi, 30.0, 50.0)
     cfg = g.fp_config()
     assert cfg["kernel"] == 3 and cfg["y_fastest_x_march"]
     x = torch.rand((B, 8, 8, 8), device=DEV, generator=torch.Generator(device=DEV).manual_seed(3))
@@ -512,7 +516,9 @@ def test_many_views_times_batch_splits_tma_launches(ops):
     a = ops.adjoint(y, g)
     for i in (0, 20, 21, 24):
         assert torch.equal(p[i], ops.forward_project(x[i].contiguous(), g)), i
-        assert rel_l2(host(a[i]), host(ops.adjoint(y[i].contiguous(), g))) <= 1e-6, i
+        want = oracle.adjoint(og, host(y[i]))
+        assert rel_l2(host(a[i]), want) <= 1e-5, i
+        assert rel_l2(host(ops.adjoint(y[i].contiguous(), g)), want) <= 1e-5, i
 
 
 def test_misaligned_pointer_is_rejected(ops):
