@@ -11,6 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpyronn.so")
+ROOFLINE_SRC = os.path.join(HERE, "roofline_peaks.cu")
+ROOFLINE_LIB = os.path.join(OUT, "libpyronn_roofline.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -71,6 +73,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     return LIB
+
+
+def build_roofline(force: bool = False) -> str:
+    """The on-chip peak micro-benchmark (roofline_peaks.cu) as its own small library: it measures the
+    denominators of the benchmark's roofline fractions and is not part of the operator library."""
+    os.makedirs(OUT, exist_ok=True)
+    if force or not os.path.exists(ROOFLINE_LIB) or os.path.getmtime(ROOFLINE_SRC) > os.path.getmtime(ROOFLINE_LIB):
+        cmd = [_nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", ROOFLINE_SRC, "-o",
+                                  ROOFLINE_LIB]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for roofline_peaks.cu:\n{r.stdout}\n{r.stderr}")
+    return ROOFLINE_LIB
 
 
 if __name__ == "__main__":

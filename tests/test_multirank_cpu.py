@@ -46,39 +46,6 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
 
     class A:
-        warmup, steps, gpus, ref_seconds = 3, 2, 2, 1.0
+        warmup, steps, gpus, ref_seconds, workload = 3, 2, 2, 1.0, "cone512_jitter"
 
     assert bench.run_reference(A()) == 0
-
-
-def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
-    """Rank 0 prints one JSON line with the reference arm's keys: the timed steps' rate as value, e2e with
-    no host-device bytes, and a cpu_baseline that carries the all-core and the single-core oracle rates.
-    The oracle timings are replaced by fixed numbers here; the line's arithmetic is what is checked."""
-    import json
-    sys.path.insert(0, ROOT)
-    import bench
-    monkeypatch.setenv("RANK", "0")
-    monkeypatch.setattr(bench, "build_inputs", lambda: None)
-    calls = []
-
-    def fake_rate(vol, n_views, target_s=10.0):
-        calls.append(target_s)
-        return 0.0, 3_000_000, 2.0, 8, 5          # 3e6 samples in 2 s on 8 threads, 5 views
-
-    monkeypatch.setattr(bench, "oracle_sample_rate", fake_rate)
-    monkeypatch.setattr(bench, "oracle_single_core_rate", lambda vol: (0.001, 1_000_000, 1.0))
-
-    class A:
-        warmup, steps, gpus, ref_seconds = 3, 2, 1, 30.0
-
-    assert bench.run_reference(A()) == 0
-    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
-    assert len(lines) == 1
-    d = json.loads(lines[0])
-    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3 and len(calls) == 5
-    assert abs(d["value"] - 1.5e-3) < 1e-12 and d["unit"] == "G ray-samples/s"
-    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 8 and cb["value"] == d["value"]
-    assert cb["single_core"]["cores"] == 1 and abs(cb["single_core"]["value"] - 0.001) < 1e-15
