@@ -8,10 +8,12 @@
 // so that for a voxel at index offset d from the centre u = u0 + (Qa . d) / w, v = v0 + (Qb . d) / w,
 // w = w0 + Pw . d. Every FP32 quantity is of the size of the brick's footprint, so the bilinear
 // weights carry ~1e-6-pixel errors instead of the ~1e-5 of absolute FP32 detector coordinates.
-// Along the column the three numerators advance by one addition each; when a view's u and w do
-// not depend on z (circular orbits) only v is recomputed, and where every voxel of a warp's columns
-// reads all four taps on the detector (each lane tests its column's end voxels, the warp votes) the
-// warp reads them without bounds tests.
+// When a view's u and w do not depend on z (circular orbits) only v is recomputed along a column;
+// otherwise (tilted detectors, arbitrary trajectories) u, v and 1/w are formed per voxel. In both
+// cases u and v are monotone along a column, so where every voxel of a warp's columns reads all four
+// taps on the detector (each lane tests its column's end voxels, the warp votes) the warp reads them
+// without bounds tests; other warps take the checked path, whose numerators advance by one addition
+// per voxel.
 #include "device_common.cuh"
 
 namespace pyronn {
@@ -188,6 +190,45 @@ __device__ __forceinline__ void bp_brick(const OpParams &p, const T *__restrict_
                     acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
                 }
             } else {
+                // General views (u and w vary along z: tilted detectors, arbitrary trajectories). Along a
+                // column, u(z) = (na + z Qa_z) / (w + z Pw_z) and v(z) are ratios of linear functions whose
+                // denominator stays positive when it is positive at both ends, hence monotone: the end
+                // voxels bound the column. Lanes whose columns lie on the detector with a margin of 1e-3
+                // pixel (far above the rounding of these small quantities) read their taps without bounds
+                // tests when the whole warp does; positions are formed per z from the column's start.
+                {
+                    const float zl = (float)(BZ - 1);
+                    const float w1 = fmaf(zl, V.Pw[2], w);
+                    const bool wpos = w > 0.0f && w1 > 0.0f;
+                    const float iw0 = wpos ? __frcp_rn(w) : 0.0f, iw1 = wpos ? __frcp_rn(w1) : 0.0f;
+                    const float qu0 = fmaf(na, iw0, V.fu), qu1 = fmaf(fmaf(zl, V.Qa[2], na), iw1, V.fu);
+                    const float qv0 = fmaf(nb, iw0, V.fv), qv1 = fmaf(fmaf(zl, V.Qb[2], nb), iw1, V.fv);
+                    const float eps = 1e-3f;
+                    const float lu = -(float)V.U0 + eps, hu = (float)(nu - 1 - V.U0) - eps;
+                    const float lv = -(float)V.V0 + eps, hv = (float)(nv - 1 - V.V0) - eps;
+                    const bool ok = wpos && qu0 >= lu && qu0 < hu && qu1 >= lu && qu1 < hu && qv0 >= lv && qv0 < hv &&
+                                    qv1 >= lv && qv1 < hv;
+                    if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+                        for (int z = 0; z < BZ; ++z) {
+                            const float fz = (float)z;
+                            const float iw = __frcp_rn(fmaf(fz, V.Pw[2], w));
+                            const float qu = fmaf(fmaf(fz, V.Qa[2], na), iw, V.fu);
+                            const float qv = fmaf(fmaf(fz, V.Qb[2], nb), iw, V.fv);
+                            const float tu = __fadd_rd(qu, 12582912.0f), tv = __fadd_rd(qv, 12582912.0f);
+                            const float au = qu - (tu - 12582912.0f), av = qv - (tv - 12582912.0f);
+                            const T *r = q + ((__float_as_int(tv) - 0x4B400000 + V.V0) * nu +
+                                              (__float_as_int(tu) - 0x4B400000 + V.U0));
+                            const float q00 = ldg_f32(r), q01 = ldg_f32(r + 1);
+                            const float q10 = ldg_f32(r + nu), q11 = ldg_f32(r + nu + 1);
+                            const float r0 = fmaf(au, q01 - q00, q00);
+                            const float r1 = fmaf(au, q11 - q10, q10);
+                            const float om = W2 ? iw * iw : 1.0f;
+                            acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
+                        }
+                        continue;
+                    }
+                }
 #pragma unroll
                 for (int z = 0; z < BZ; ++z) {
                     if (w > 0.0f) {
