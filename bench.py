@@ -173,13 +173,16 @@ def build_volume(name: str, rank: int = 0) -> np.ndarray:
                                        (0.5, 0.5, 0.5))
 
 
-def make_geometry(name: str):
+def make_geometry(name: str, views: int | None = None):
+    """The workload's geometry; views: keep only that many of its views, evenly spaced (profiling runs)."""
     from paper_2511_08427_gb300.operators import Geometry
     if name == "cone512_jitter":
         tr = trajectory()
-        return Geometry.cone_from_positions((512, 512, 512), (0.4, 0.4, 0.4), (1024, 1024), (0.4, 0.4), tr.src,
-                                            tr.det_centre, tr.eu, tr.ev)
-    return Geometry.cone_circular((256, 256, 256), (0.5, 0.5, 0.5), (512, 512), (0.6, 0.6), 360, 2 * math.pi,
+        idx = np.arange(720) if views is None else np.linspace(0, 719, views).round().astype(int)
+        return Geometry.cone_from_positions((512, 512, 512), (0.4, 0.4, 0.4), (1024, 1024), (0.4, 0.4), tr.src[idx],
+                                            tr.det_centre[idx], tr.eu[idx], tr.ev[idx])
+    n = 360 if views is None else views
+    return Geometry.cone_circular((256, 256, 256), (0.5, 0.5, 0.5), (512, 512), (0.6, 0.6), n, 2 * math.pi * n / 360,
                                   750.0, 1200.0)
 
 
@@ -348,6 +351,9 @@ def cpu_baseline_leg(name, vol_np, g, dev, results):
             del s_dt
         torch.cuda.empty_cache()
         prec[tag] = {"fp_rel_l2": fp_err, "bp_rel_l2": bp_err, "adjoint_rel_l2": adj_err}
+    if results.get("_sino_texf") is not None:
+        prec["fp_texture_filtered_f32"] = rel(results["_sino_texf"].index_select(0, idx_dev).double().cpu().numpy(),
+                                              p_or)
     prec["note"] = "None: the output exceeds the storage type's range (FP16 saturates above 65504)"
     prec["samples"] = {"fp": f"{nv} whole views ({samples} samples)", "bp": f"{vids.size} random voxels",
                        "adjoint": f"sparse cotangent on {rids.size} random rays, whole volume compared"}
@@ -607,6 +613,17 @@ def run_gpu(args):
     big = vol_np.nbytes > 200 * 2 ** 20
     flush = None if big else torch.empty(256 * 1024 * 1024 // 4, device=dev)
 
+    # tile and brick shapes chosen by the library's autotuner on a subset of the views (the per-view work
+    # is the same; the whole geometry would take a minute of timing), applied to the full geometry
+    from paper_2511_08427_gb300 import autotune
+    tuned = {}
+    g_sub = make_geometry(name, views=max(1, V // 8))
+    for op in ("fp", "adjoint", "bp"):
+        r = autotune.tune(g_sub, op, repeats=2, use_cache=False, device=dev)
+        autotune.apply(g, autotune.OPS[op], *r["params"])
+        tuned[op] = {"params": r["params"], "subset_ms": r["ms"], "candidates": r["candidates"],
+                     "subset_views": g_sub.n_views}
+    del g_sub
     rates = roofline.measure()   # on-chip peaks per SM clock, measured on this GPU before the timed region
     timed_steps(ops, g, vol, sino, cot, adj, bpv, args.warmup, stream, torch, flush)
     if world > 1:
@@ -647,6 +664,30 @@ def run_gpu(args):
     e2e_rate = job_rate(n_samples, world, 1, e2e_s)
     del h_vol, h_sino
 
+    # the hardware-filtered texture projector (opt-in variant 5: the texture unit's 8-bit trilinear
+    # weights, not the FP32 operator) on the same workload; its error is measured in the CPU leg
+    g.set_variant(0, 5)
+    texf = None
+    if g.fp_config()["kernel"] == 5:
+        sino_tf = torch.empty((V, nv, nu), device=dev)
+        ops.forward_project(vol, g, out=sino_tf)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            ops.forward_project(vol, g, out=sino_tf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tf_ms = e0.elapsed_time(e1) / 3
+        texf = {"ms": tf_ms, "gsamples_per_s": n_samples / (tf_ms * 1e-3) / 1e9,
+                "texture_unit": {"achieved_gfetch_per_s": n_samples / (tf_ms * 1e-3) / 1e9,
+                                 "peak_gfetch_per_s": rates["tex3d_trilinear_per_clk_sm"] * rates["sms"] * mhz / 1e3,
+                                 "frac": n_samples / (tf_ms * 1e-3) / (rates["tex3d_trilinear_per_clk_sm"] *
+                                                                     rates["sms"] * mhz * 1e6)},
+                "note": "opt-in approximation (8-bit interpolation fractions of the texture unit); includes the "
+                        "copy of the volume into the 3D texture"}
+    g.set_variant(0, 0)
+
     # kernels of one step: FP (plus the y-fastest copy it stages x-march slabs from), adjoint, BP
     fpc = g.fp_config()
     launches_per_step = 3 + (1 if fpc["kernel"] == 3 and fpc["y_fastest_x_march"] else 0)
@@ -669,15 +710,21 @@ def run_gpu(args):
         "roofline": dominant,
         "rooflines": rl,
         "onchip_peaks": dict(rates, source="roofline_peaks.cu, measured in this run before the timed region"),
+        "autotune": dict(tuned, params="fp: (slab depth, buffers); adjoint: (slab depth, pitch mode); bp: (brick "
+                                       "depth, -)"),
+        "fp_texture_filtered": texf,
         "hbm": {"compulsory_gb_per_step": (3 * vol_np.nbytes + 3 * V * nv * nu * 4) / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"), "peak_source": peak_src},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        results = {"_sino": sino, "_vol": vol, "samples_per_fp": n_samples, "updates_per_bp": n_updates}
+        results = {"_sino": sino, "_vol": vol, "samples_per_fp": n_samples, "updates_per_bp": n_updates,
+                   "_sino_texf": sino_tf if texf else None}
         base, prec = cpu_baseline_leg(name, vol_np, g, dev, results)
         result["cpu_baseline"] = base
         result["precision"] = prec
     del sino, cot, adj, bpv, vol
+    if texf:
+        del sino_tf
     torch.cuda.empty_cache()
     if name == HEADLINE and not args.no_secondary:
         result["cone256"] = run_cone256(dev, max(3, K // 2), rates, mhz)
@@ -687,6 +734,48 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_profile(args):
+    """One operator of a workload, a few launches after one warm-up launch (for Nsight Compute): fp, adj
+    (matched adjoint of a standard-normal cotangent), bp (voxel-driven), fbp (filter). --views keeps a
+    subset of the views so that a capture of many passes stays small. --time prints the mean CUDA-event
+    time per launch."""
+    import torch
+    from paper_2511_08427_gb300 import operators as ops
+    dev = torch.device("cuda", 0)
+    dt = getattr(torch, args.dtype)
+    g = make_geometry(args.workload, args.views)
+    vol = torch.from_numpy(build_volume(args.workload)).to(dev).to(dt)
+    sshape = (g.n_views,) + tuple(g.detector_shape)
+    sino = torch.empty(sshape, device=dev, dtype=dt)
+    out2 = torch.empty_like(sino) if args.profile == "fbp" else None
+    if args.profile != "fp":
+        sino.copy_(torch.randn(sshape, device=dev, generator=torch.Generator(device=dev).manual_seed(22)))
+
+    def run():
+        if args.profile == "fp":
+            ops.forward_project(vol, g, out=sino)
+        elif args.profile == "adj":
+            ops.adjoint(sino, g, out=vol)
+        elif args.profile == "fbp":
+            ops.fbp_filter(sino, g, out=out2)
+        else:
+            ops.back_project(sino, g, out=vol)
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.repeat):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    msg = f"{args.profile} {args.workload} views={g.n_views} {args.dtype}"
+    if args.time:
+        msg += f": {e0.elapsed_time(e1) / args.repeat:.3f} ms per launch"
+    print(msg, "flags", g.read_flags(), flush=True)
     return 0
 
 
@@ -701,7 +790,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--profile", choices=["fp", "adj", "bp", "fbp"], default=None,
+                    help="run one operator of --workload for a profiler instead of the benchmark")
+    ap.add_argument("--views", type=int, default=None, help="--profile: keep this many of the workload's views")
+    ap.add_argument("--repeat", type=int, default=2, help="--profile: launches after the warm-up launch")
+    ap.add_argument("--dtype", default="float32", choices=["float32", "bfloat16", "float16"])
+    ap.add_argument("--time", action="store_true", help="--profile: print the mean time per launch")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

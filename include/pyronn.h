@@ -310,14 +310,20 @@ PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void 
  * 3 slab-staged kernel filled by TMA tensor copies (needs a row pitch that is a multiple of 16
  * bytes; falls back to 2), 4 one thread per ray with texture gathers from a tiled 2D copy of the
  * volume (3D FP32 within the device's gather-texture limits, else as 0; the copy belongs to the
- * geometry, so forward projections with one geometry on different streams must not overlap).
+ * geometry, so forward projections with one geometry on different streams must not overlap), 5 one
+ * thread per ray with the texture unit's trilinear filtering from a geometry-owned 3D texture copy of
+ * the volume (the paper's "texture interpolation", Sec. 2.1: FP32 or FP16 storage of 3D volumes within
+ * the device's 3D texture limits, else as 0; the hardware weighs the texels with 8-bit fractions, so
+ * this variant is NOT the library's operator to FP32 accuracy but an approximation of it with a
+ * relative error of the order of 1e-3; same stream restriction as variant 4).
  * op 1 = matched adjoint:
  * variant 0 automatic (= 3 where its box fits, else 2), 1 one-thread-per-ray FP32 global atomics,
  * 2 output-stationary bricks accumulated in shared memory, 3 slab-ordered: detector tiles march
  * the volume like the forward projector, scatter into shared-memory slab boxes and add each box to
  * the volume with vector reductions. op 2 = voxel-driven back-projection: variant 0 automatic
  * (= 2), 1 one thread per voxel in absolute detector coordinates, 2 bricks with detector
- * coordinates relative to the brick centre's projection. All variants compute the same operator. */
+ * coordinates relative to the brick centre's projection. All variants compute the same operator,
+ * except forward-projection variant 5 (approximate interpolation weights). */
 PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
 
 /* Tuning knobs of the kernels (used by the autotuner; 0 restores the automatic choice). All
@@ -338,16 +344,42 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * the rays of a warp, which spread across y there, read consecutive shared-memory words; 1 stages
  * every slab from the volume itself; PYRONN_TUNE_ADJ_PITCH: 0 (automatic) gives the slab-ordered
  * adjoint's x-march boxes an odd row pitch (one word more than their x extent) wherever a slab depth
- * still fits two CTAs per SM with it, 1 keeps rows of whole 16-byte groups. */
+ * still fits two CTAs per SM with it, 1 keeps rows of whole 16-byte groups; PYRONN_TUNE_ADJ_DEPTH: slab
+ * depth of the slab-ordered adjoint in voxel planes, 2 .. 16 (0 automatic: the deepest of 8, 6, 5, 4 whose
+ * box lets two CTAs share an SM; a depth whose box does not fit runs one CTA per SM, or the brick adjoint
+ * if the box exceeds 160 KB); PYRONN_TUNE_BP_BRICK_Z: voxels per thread along z of the brick
+ * back-projector of 3D volumes, 4, 8 or 16 (0 automatic = 8); PYRONN_TUNE_ADJ_LANES: how the
+ * slab-ordered adjoint's lanes take the pixels of a tile, 0 automatic (= 1), 1 the 32 lanes of a warp on
+ * consecutive pixels of one tile row, 2 in each pass on every other pixel of two rows two pixels apart
+ * (rays of adjacent pixels often share a cell, and their reductions then hit the same shared word). */
 typedef enum {
     PYRONN_TUNE_FP_DEPTH = 0,
     PYRONN_TUNE_FP_BUFFERS = 1,
     PYRONN_TUNE_ADJ_ACCUM = 2,
     PYRONN_TUNE_FP_CTAS_PER_SM = 3,
     PYRONN_TUNE_FP_TRANSPOSE = 4,
-    PYRONN_TUNE_ADJ_PITCH = 5
+    PYRONN_TUNE_ADJ_PITCH = 5,
+    PYRONN_TUNE_ADJ_DEPTH = 6,
+    PYRONN_TUNE_BP_BRICK_Z = 7,
+    PYRONN_TUNE_ADJ_LANES = 8
 } pyronn_tuning_param;
 PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
+
+/* Autotuner (the batched pattern's tile and brick shapes chosen by measurement; the paper has no
+ * dedicated passage): times every candidate configuration of one operator of g that runs on the kernel
+ * it tunes, with CUDA events on `stream` after one warm-up launch each, and applies the fastest through
+ * pyronn_geom_set_tuning (the choice stays with g). op 0: forward projection, in = volume, out =
+ * sinogram; candidates (slab depth, buffers) of the TMA-staged projector. op 1: matched adjoint,
+ * in = sinogram, out = volume; candidates (slab depth, pitch mode) of the slab-ordered adjoint. op 2:
+ * voxel-driven back-projection (plain weights), in = sinogram, out = volume; candidates: brick depth
+ * 4, 8, 16 (3D). Buffers hold one batch item of dtype (device memory, 16-byte aligned); out is
+ * overwritten, in is only read; nothing is allocated beyond what the operators allocate on first use.
+ * repeats: timed launches per candidate (1 .. 1000). result[4]: mean milliseconds per launch of the
+ * chosen candidate, its two parameters (op 2: brick depth, 0) and the number of candidates timed.
+ * Synchronises the stream. PYRONN_INVALID_ARG if no candidate applies (the knobs are then left as
+ * they were). */
+PYRONN_API int pyronn_autotune(pyronn_geom_t g, int op, const void *in, void *out, int dtype, int repeats,
+                               void *stream, double *result);
 
 /* ------------------------------------------------------------------------------------------
  * Diagnostics.
@@ -364,7 +396,7 @@ PYRONN_API int pyronn_geom_read_flags(pyronn_geom_t g, int *out, int reset);
 
 /* Forward-projector configuration that would be used for element type dtype (host computation,
  * no GPU needed), 20 ints: [0] kernel (1 direct, 2 slab thread-staged, 3 slab TMA-staged, 4 texture
- * gather),
+ * gather, 5 hardware-filtered texture),
  * [1] slab depth, [2] guard planes, [3] first slab plane, [4..12] TMA box (x, y, z) for march
  * axes x, y, z, [13] elements per TMA buffer, [14] dynamic shared memory bytes per CTA,
  * [15] thread-staged box capacity (elements), [16] 1 if x-march boxes are staged from the y-fastest

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("pyronn_geom_get_views", _c_int, [_vp, _dp]),
     ("pyronn_geom_count_samples", _c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
     ("pyronn_geom_set_variant", _c_int, [_vp, _c_int, _c_int]),
+    ("pyronn_autotune", _c_int, [_vp, _c_int, _vp, _vp, _c_int, _c_int, _vp, _dp]),
     ("pyronn_geom_set_tuning", _c_int, [_vp, _c_int, _c_int]),
     ("pyronn_fp", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("pyronn_adjoint", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),

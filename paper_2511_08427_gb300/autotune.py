@@ -1,13 +1,16 @@
-"""Autotuner for the kernel knobs of a geometry (slab depth and buffer count of the TMA-staged
-forward projector).
+"""Front end of the library's autotuner (pyronn_autotune): tile and brick shapes chosen by measurement.
 
-Every candidate computes the same operator; the tuner times each with CUDA events on the current
-stream (after a warm-up launch) and keeps the fastest. Results are cached in a JSON file keyed by
-the device name and a signature of the geometry (shapes, spacings, views, step, element type), so
-a later process re-applies the choice without timing.
+``tune(g, op)`` lets the library time every candidate configuration of one operator of a geometry
+(forward projection: slab depth x buffers of the TMA-staged projector; matched adjoint: slab depth x
+row pitch of the slab-ordered adjoint; back-projection: brick depth) with CUDA events on the current
+stream and apply the fastest. The choice is cached in a JSON file keyed by the device name, the
+operator and a signature of the geometry (shapes, spacings, views, step, element type), so a later
+process re-applies it through pyronn_geom_set_tuning without timing. Every candidate computes the same
+operator.
 """
 from __future__ import annotations
 
+import ctypes
 import hashlib
 import json
 import os
@@ -15,10 +18,13 @@ import os
 import numpy as np
 import torch
 
-from ._lib import PyronnError
-from .operators import TUNE_FP_BUFFERS as FP_BUFFERS, TUNE_FP_DEPTH as FP_DEPTH
+from . import _lib
+from .operators import (_DTYPES, TUNE_ADJ_DEPTH, TUNE_ADJ_PITCH, TUNE_BP_BRICK_Z, TUNE_FP_BUFFERS,
+                        TUNE_FP_DEPTH)
 
-DEFAULT_CANDIDATES = [(8, 2), (8, 1), (4, 2), (4, 1), (12, 1), (16, 1)]
+OPS = {"fp": 0, "adjoint": 1, "bp": 2}
+# the two tuning knobs each operator's result sets (the second is unused for the back-projector)
+_KNOBS = {0: (TUNE_FP_DEPTH, TUNE_FP_BUFFERS), 1: (TUNE_ADJ_DEPTH, TUNE_ADJ_PITCH), 2: (TUNE_BP_BRICK_Z, None)}
 
 
 def _cache_path() -> str:
@@ -52,52 +58,46 @@ def _store(db):
         pass
 
 
-def apply(g, depth: int, nbuf: int) -> None:
-    g.set_tuning(FP_DEPTH, int(depth))
-    g.set_tuning(FP_BUFFERS, int(nbuf))
+def apply(g, op: int, a: int, b: int) -> None:
+    k1, k2 = _KNOBS[op]
+    g.set_tuning(k1, int(a))
+    if k2 is not None:
+        g.set_tuning(k2, int(b))
 
 
-def tune_forward(g, dtype=torch.float32, candidates=None, repeats: int = 3, use_cache: bool = True,
-                 device=None) -> dict:
-    """Time the forward projector for each (depth, buffers) candidate and apply the fastest.
+def tune(g, op: str = "fp", dtype=torch.float32, repeats: int = 2, use_cache: bool = True, device=None) -> dict:
+    """Tune one operator ('fp', 'adjoint' or 'bp') of geometry g and apply the choice.
 
-    Returns {"depth", "buffers", "ms", "timings": {...}, "cached": bool}.
-    """
-    from . import operators as ops
+    Returns {"op", "params": [a, b], "ms", "candidates", "cached"}. The timing buffers are allocated here
+    (torch) and freed on return; the library allocates nothing for the tuning itself."""
+    o = OPS[op]
     device = torch.device(device or "cuda")
-    key = torch.cuda.get_device_name(device) + "|" + signature(g, dtype)
+    key = "|".join([torch.cuda.get_device_name(device), op, signature(g, dtype)])
     db = _load() if use_cache else {}
     if use_cache and key in db:
         best = db[key]
-        apply(g, best["depth"], best["buffers"])
+        apply(g, o, *best["params"])
         return dict(best, cached=True)
     vol = torch.zeros(g.volume_shape, dtype=dtype, device=device)
-    sino = torch.empty(g.sinogram_shape, dtype=dtype, device=device)
-    stream = torch.cuda.current_stream(device)
-    timings = {}
-    for depth, nbuf in (candidates or DEFAULT_CANDIDATES):
-        try:
-            apply(g, depth, nbuf)
-            if g.fp_config(dtype)["kernel"] != 3:
-                continue
-            ops.forward_project(vol, g, out=sino)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            ev[0].record(stream)
-            for _ in range(repeats):
-                ops.forward_project(vol, g, out=sino)
-            ev[1].record(stream)
-            torch.cuda.synchronize(device)
-            timings[f"{depth}x{nbuf}"] = ev[0].elapsed_time(ev[1]) / repeats
-        except PyronnError:
-            continue
-    if not timings:
-        apply(g, 0, 0)
-        return {"depth": 0, "buffers": 0, "ms": None, "timings": {}, "cached": False}
-    best_key = min(timings, key=timings.get)
-    depth, nbuf = (int(x) for x in best_key.split("x"))
-    apply(g, depth, nbuf)
-    best = {"depth": depth, "buffers": nbuf, "ms": timings[best_key], "timings": timings}
+    sino = torch.zeros(g.sinogram_shape, dtype=dtype, device=device)
+    if o == 0:
+        vol.uniform_(0.0, 1.0)
+        src, dst = vol, sino
+    else:
+        sino.normal_()
+        src, dst = sino, vol
+    res = (ctypes.c_double * 4)()
+    stream = torch.cuda.current_stream(device).cuda_stream
+    _lib.check(_lib.lib().pyronn_autotune(g.handle, o, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                          _DTYPES[dtype], int(repeats), ctypes.c_void_p(stream), res))
+    best = {"op": op, "params": [int(res[1]), int(res[2])], "ms": float(res[0]), "candidates": int(res[3])}
     if use_cache:
         db[key] = best
         _store(db)
     return dict(best, cached=False)
+
+
+def tune_forward(g, dtype=torch.float32, repeats: int = 2, use_cache: bool = True, device=None) -> dict:
+    """Forward projector only (slab depth and buffer count); {"depth", "buffers", "ms", "cached"}."""
+    r = tune(g, "fp", dtype, repeats, use_cache, device)
+    return {"depth": r["params"][0], "buffers": r["params"][1], "ms": r["ms"], "cached": r["cached"]}

@@ -18,6 +18,28 @@
 
 namespace pyronn {
 
+int stride_grid(long long n, int ctas_per_sm) {
+    static std::mutex mu;
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = -1;
+    int count = 0;
+    if (dev >= 0) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (sms[dev] == 0 && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms[dev] = 0;
+        count = sms[dev];
+    }
+    if (count <= 0) count = 1;
+    const long long need = (n + 255) / 256;
+    const long long cap = (long long)count * ctas_per_sm;
+    return (int)(need < 1 ? 1 : (need < cap ? need : cap));
+}
+
+}  // namespace pyronn
+
+namespace pyronn {
+
 static thread_local std::string g_last_error;
 
 int set_error(int code, const char *fmt, ...) {
@@ -582,7 +604,7 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
     if (!g) return PYRONN_OK;
     // device buffers are freed on the device they were allocated on
     if (g->d_fp || g->d_scratch || g->d_stage_in || g->d_stage_out || g->d_upd_sino || g->d_upd_vol || g->d_fbp ||
-        g->d_vol_t || g->copy_stream || g->tex_arr) {
+        g->d_vol_t || g->copy_stream || g->tex_arr || g->texf_arr) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (g->device >= 0 && g->device != cur) cudaSetDevice(g->device);
@@ -603,6 +625,8 @@ int pyronn_geom_destroy(pyronn_geom_t g) {
         if (g->tex_obj) cudaDestroyTextureObject((cudaTextureObject_t)g->tex_obj);
         if (g->tex_arr) cudaFreeArray((cudaArray_t)g->tex_arr);
         cudaFree(g->d_tex_org);
+        if (g->texf_obj) cudaDestroyTextureObject((cudaTextureObject_t)g->texf_obj);
+        if (g->texf_arr) cudaFreeArray((cudaArray_t)g->texf_arr);
         if (g->device >= 0 && cur >= 0 && g->device != cur) cudaSetDevice(cur);
     }
     delete g;

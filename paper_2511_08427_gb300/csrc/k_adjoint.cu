@@ -73,7 +73,7 @@ static int launch_t(const OpParams &p, const void *sino, float *acc, void *vol, 
     }
     if ((void *)acc != vol) {
         long long n = p.vol_elems * p.batch;
-        int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+        int blocks = stride_grid(n, 16);
         convert_from_f32_kernel<T><<<blocks, 256, 0, st>>>(acc, (T *)vol, n);
     }
     return (int)cudaGetLastError();
@@ -93,7 +93,7 @@ static int launch_via_acc_t(const OpParams &p, const void *sino, float *acc, voi
                                                           acc + b0 * p.vol_elems);
     }
     long long n = p.vol_elems * p.batch;
-    int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    int blocks = stride_grid(n, 16);
     convert_from_f32_kernel<T><<<blocks, 256, 0, st>>>(acc, (T *)vol, n);
     return (int)cudaGetLastError();
 }

@@ -376,7 +376,21 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
     const int base0 = -1;
     const int nslab_all = (Nm + 1 - base0 + D - 1) / D;
 
-    // rays of this thread: tile row warp * AS_RPT + j, lanes along u
+    // rays of this thread (pixel (u, v) of ray j): cfg.lanes 0: tile row warp * AS_RPT + j, lanes along u;
+    // cfg.lanes 1: the warp's 32 x 4 pixel block taken so that in each pass j the lanes sit on every other
+    // pixel of two rows two pixels apart (u = 2 (lane mod 16) + (j & 1), v = 2 (lane / 16) + (j >> 1)).
+    // Neighbouring pixels are often less than a voxel apart in the volume, so lanes on adjacent pixels
+    // share cells and their reductions hit the same word; two pixels apart they rarely do.
+    const int lanes_mode = cfg.lanes;
+    auto pixel = [&](int j, int &u, int &v) {
+        if (lanes_mode) {
+            u = tu0 + 2 * (lane & 15) + (j & 1);
+            v = tv0 + warp * AS_RPT + 2 * (lane >> 4) + (j >> 1);
+        } else {
+            u = tu0 + lane;
+            v = tv0 + warp * AS_RPT + j;
+        }
+    };
     // per-ray state kept across slabs: value y dt (0: nothing to scatter), and the global FP32 ray's
     // march-axis coordinate, inverse step and sample range, which define the slab partition
     float yv[AS_RPT], rcm[AS_RPT], rinv[AS_RPT];
@@ -385,7 +399,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
     unsigned ybits = 0u;
 #pragma unroll
     for (int j = 0; j < AS_RPT; ++j) {
-        const int u = tu0 + lane, v = tv0 + warp * AS_RPT + j;
+        int u, v;
+        pixel(j, u, v);
         float yj = 0.0f;
         if (u <= tu1 && v <= tv1) {
             const long long o = (long long)v * p.det.nu + u;
@@ -406,7 +421,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
 #pragma unroll
     for (int j = 0; j < AS_RPT; ++j) {
         if (yv[j] == 0.0f) continue;
-        const int u = tu0 + lane, v = tv0 + warp * AS_RPT + j;
+        int u, v;
+        pixel(j, u, v);
         const RayIdx r = ray_setup(rec, p.vol, (float)u, (float)v);
         int k0, k1;
         if (!ray_k_range(r, p.vol, dt, k0, k1)) {
@@ -540,7 +556,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         for (int j = 0; j < AS_RPT; ++j) {
             const float y = yv[j];
             if (y == 0.0f) continue;   // rays outside the detector or the volume, zero values, direct rays
-            const int u = tu0 + lane, v = tv0 + warp * AS_RPT + j;
+            int u, v;
+            pixel(j, u, v);
             // slab partition on the global FP32 ray (identical formula for the shared boundaries)
             const float cm = rcm[j], inv_step = rinv[j];
             int ka, kb;
@@ -791,8 +808,11 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, AdjS
     __shared__ AsShared sh;
     AsSlab *slabs = reinterpret_cast<AsSlab *>(box + ((cfg.box_cap + 3) & ~3));
     as_zero_box(box, cfg.box_cap);
-    as_tile<T>(p, cfg, sino, sino_b, y_scale, vol, blockIdx.z % p.n_views, blockIdx.z / p.n_views, blockIdx.x,
-               blockIdx.y, box, slabs, sh);
+    // grid (tile columns, views, tile rows x batch items), in the order that keeps the volume band of
+    // one tile row in L2 while the resident CTAs reduce into it (see the launcher)
+    const int ntv = (p.det.nv + AS_TV - 1) / AS_TV;
+    as_tile<T>(p, cfg, sino, sino_b, y_scale, vol, blockIdx.y, blockIdx.z / ntv, blockIdx.x, blockIdx.z % ntv, box,
+               slabs, sh);
 }
 
 // Persistent launch over the (view, tile) items of several volumes (each with its own geometry and
@@ -914,9 +934,10 @@ size_t adjoint_slab_smem_bytes(int box_cap, int max_slabs) {
     return sizeof(float) * (size_t)((box_cap + 3) & ~3) + sizeof(AsSlab) * (size_t)max_slabs;
 }
 
-// Deepest slab (8, 6, 5 or 4 planes) whose box and slab table let two CTAs share an SM (224 KB of
-// shared memory, 1 KB reserved per CTA, the static tile state), first with the odd row pitch of x-march
-// boxes, then without it; otherwise the shallowest whose box fits in 160 KB (16-byte pitch).
+// Deepest slab (8, 6, 5 or 4 planes; or the depth set by PYRONN_TUNE_ADJ_DEPTH) whose box and slab table
+// let two CTAs share an SM (224 KB of shared memory, 1 KB reserved per CTA, the static tile state), first
+// with the odd row pitch of x-march boxes, then without it; otherwise the last one tried (16-byte pitch)
+// if its box fits in 160 KB (one CTA per SM).
 AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     AdjSlabCfg c{};
     if (g->ndim != 3) return c;
@@ -930,8 +951,12 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     const long long hard = (160 * 1024) / 4;
     long long need = 0;
     bool fit = false;
+    const int forced = g->tuning.adj_depth;
+    const int depths[4] = {8, 6, 5, 4};
+    const int ndepths = forced > 0 ? 1 : 4;
     for (int xpad = g->tuning.adj_pitch == 1 ? 0 : 1; xpad >= 0 && !fit; --xpad)
-        for (int depth : {8, 6, 5, 4}) {
+        for (int di = 0; di < ndepths; ++di) {
+            const int depth = forced > 0 ? forced : depths[di];
             need = as_bound(g, depth, c.guard, xpad);
             c.depth = depth;
             c.xpad = xpad;
@@ -946,6 +971,7 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     c.valid = need > 0 && need <= hard && adjoint_slab_smem_bytes(c.box_cap, c.max_slabs) <= 200 * 1024;
     c.allow_fixed = g->tuning.adj_accum != 1;
     c.cell_fixed = g->tuning.adj_accum == 2;
+    c.lanes = g->tuning.adj_lanes == 2 ? 1 : 0;
     return c;
 }
 
@@ -963,7 +989,7 @@ template <typename T>
 static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sino, const void *sino_b, float y_scale,
                          bool accumulate, float *acc, void *vol, cudaStream_t st) {
     const long long n = p.vol_elems * p.batch;
-    const int cblocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    const int cblocks = stride_grid(n, 16);
     cudaError_t e = cudaSuccess;
     if (!accumulate) e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)n, st);
     else if ((void *)acc != vol) adjoint_widen_kernel<T><<<cblocks, 256, 0, st>>>((const T *)vol, acc, n);
@@ -974,13 +1000,29 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
     e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
-    const int per_launch = 65535 / p.n_views > 0 ? 65535 / p.n_views : 1;
+    // Grid order: tile columns fastest, then views, then tile rows and batch items, so that the CTAs
+    // resident at one time (the tiles of one tile row in consecutive views) reduce into one band of the
+    // volume, which stays in L2 while they do; with views outermost every view's flushes would sweep the
+    // whole volume, through DRAM once it exceeds L2. Views beyond the 65535 grid rows and batches beyond
+    // 65535 tile rows are split into several launches.
+    const int ntv = ceil_div(p.det.nv, AS_TV);
+    const int per_launch = 65535 / ntv > 0 ? 65535 / ntv : 1;
+    const long long view_elems = (long long)p.det.nv * p.det.nu;
     for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
         const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
-        dim3 grid(ceil_div(p.det.nu, AS_TU), ceil_div(p.det.nv, AS_TV), p.n_views * nb);
-        adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(
-            p, c, (const T *)sino + b0 * p.sino_elems,
-            sino_b ? (const T *)sino_b + b0 * p.sino_elems : (const T *)nullptr, y_scale, acc + b0 * p.vol_elems);
+        for (int v0 = 0; v0 < p.n_views; v0 += 65535) {
+            const int nvw = p.n_views - v0 < 65535 ? p.n_views - v0 : 65535;
+            OpParams q = p;
+            q.fp = p.fp + v0;
+            q.bp = p.bp ? p.bp + v0 : nullptr;
+            q.views64 = p.views64 ? p.views64 + (size_t)v0 * VIEW64_STRIDE : nullptr;
+            q.n_views = nvw;
+            const long long so = b0 * p.sino_elems + v0 * view_elems;
+            dim3 grid(ceil_div(p.det.nu, AS_TU), nvw, ntv * nb);
+            adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(
+                q, c, (const T *)sino + so, sino_b ? (const T *)sino_b + so : (const T *)nullptr, y_scale,
+                acc + b0 * p.vol_elems);
+        }
     }
     if ((void *)acc != vol) adjoint_convert_kernel<T><<<cblocks, 256, 0, st>>>(acc, (T *)vol, n);
     return (int)cudaGetLastError();
@@ -1004,7 +1046,7 @@ static int launch_slab_batched_t(const PlanLaunch &L, int grid, size_t smem, cud
     for (int i = 0; i < L.n; ++i) {
         if ((void *)L.v[i].acc == L.v[i].out) continue;
         const long long n = L.v[i].p.vol_elems;
-        const int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+        const int blocks = stride_grid(n, 16);
         adjoint_convert_kernel<T><<<blocks, 256, 0, st>>>(L.v[i].acc, (T *)L.v[i].out, n);
     }
     return (int)cudaGetLastError();

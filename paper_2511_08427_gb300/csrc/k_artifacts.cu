@@ -5,7 +5,7 @@
 
 namespace pyronn {
 
-static int ew_blocks(long long n) { return (int)((n + 255) / 256 < 152 * 32 ? (n + 255) / 256 : 152 * 32); }
+static int ew_blocks(long long n) { return stride_grid(n, 32); }
 
 // out[v][u] = in[v][u - s] (axis 0, one shift per row) or in[v - s][u] (axis 1, one shift per column).
 template <typename T>

@@ -171,7 +171,7 @@ static int launch_t_transpose(const OpParams &p, const void *vol, float *acc, vo
     }
     if ((void *)acc != sino) {
         long long n = p.sino_elems * p.batch;
-        int blocks = (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+        int blocks = stride_grid(n, 16);
         bp_convert_kernel<T><<<blocks, 256, 0, st>>>(acc, (T *)sino, n);
     }
     return (int)cudaGetLastError();

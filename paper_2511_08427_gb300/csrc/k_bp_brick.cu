@@ -257,10 +257,11 @@ __device__ __forceinline__ void bp_brick(const OpParams &p, const T *__restrict_
     }
 }
 
-// four CTAs per SM (64 registers): the loop is latency-bound on its L1 detector reads at three
+// four CTAs per SM (64 registers) for columns of up to 8 voxels: the loop is latency-bound on its L1
+// detector reads at three; three for 16-voxel columns (their 16 sums need more registers)
 template <typename T, int BZ, bool W2>
-__global__ void __launch_bounds__(BPB_NT, 4) bp_brick_kernel(OpParams p, const T *__restrict__ sino,
-                                                          T *__restrict__ vol) {
+__global__ void __launch_bounds__(BPB_NT, BZ > 8 ? 3 : 4) bp_brick_kernel(OpParams p, const T *__restrict__ sino,
+                                                                       T *__restrict__ vol) {
     __shared__ BpView sv[BPB_CHUNK];
     const int nbz = (p.vol.nz + BZ - 1) / BZ;
     bp_brick<T, BZ, W2>(p, sino, vol, blockIdx.x, blockIdx.y, blockIdx.z % nbz, blockIdx.z / nbz, sv);
@@ -300,12 +301,19 @@ static void launch_bpb(const OpParams &p, const void *sino, void *vol, cudaStrea
     }
 }
 
+// bz: voxels per thread along z of 3D volumes (4, 8 or 16; 0 = 8)
 template <typename T>
-static int launch_bpb_t(const OpParams &p, const void *sino, void *vol, cudaStream_t st) {
+static int launch_bpb_t(const OpParams &p, int bz, const void *sino, void *vol, cudaStream_t st) {
     const bool w2 = p.perspective && p.weight == PYRONN_BP_INV_W2;
     if (p.vol.nz == 1) {
         if (w2) launch_bpb<T, 1, true>(p, sino, vol, st);
         else launch_bpb<T, 1, false>(p, sino, vol, st);
+    } else if (bz == 4) {
+        if (w2) launch_bpb<T, 4, true>(p, sino, vol, st);
+        else launch_bpb<T, 4, false>(p, sino, vol, st);
+    } else if (bz == 16) {
+        if (w2) launch_bpb<T, 16, true>(p, sino, vol, st);
+        else launch_bpb<T, 16, false>(p, sino, vol, st);
     } else {
         if (w2) launch_bpb<T, 8, true>(p, sino, vol, st);
         else launch_bpb<T, 8, false>(p, sino, vol, st);
@@ -338,12 +346,12 @@ int bp_brick_batched_occupancy(int *blocks_per_sm) {
                                                               BPB_NT, 0);
 }
 
-int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream) {
+int launch_bp_brick(const OpParams &p, int bz, const void *sino, void *vol, int dtype, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     switch (dtype) {
-        case PYRONN_F32: return launch_bpb_t<float>(p, sino, vol, st);
-        case PYRONN_BF16: return launch_bpb_t<__nv_bfloat16>(p, sino, vol, st);
-        case PYRONN_F16: return launch_bpb_t<__half>(p, sino, vol, st);
+        case PYRONN_F32: return launch_bpb_t<float>(p, bz, sino, vol, st);
+        case PYRONN_BF16: return launch_bpb_t<__nv_bfloat16>(p, bz, sino, vol, st);
+        case PYRONN_F16: return launch_bpb_t<__half>(p, bz, sino, vol, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -404,8 +404,12 @@ __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_kernel(OpParams p, FpTmaB
     fp_tma_buffers<T>(smem_raw, cfg.buf_elems, cfg.nbuf, buf0, buf1);
     fp_tma_init_bars(sh);
     unsigned ph[2] = {0u, 0u};
-    fp_tma_tile<T>(p, cfg, maps.map, vol, sino, blockIdx.z % p.n_views, blockIdx.z / p.n_views, blockIdx.x,
-                   blockIdx.y, buf0, buf1, sh, ph);
+    // grid (tile columns, views, tile rows x batch items): consecutive CTAs take the tiles of one tile row
+    // in consecutive views, whose rays cross the same band of the volume, so the band stays in L2 while
+    // the resident CTAs read it (see the launcher)
+    const int ntv = (p.det.nv + TMA_TV - 1) / TMA_TV;
+    fp_tma_tile<T>(p, cfg, maps.map, vol, sino, blockIdx.y, blockIdx.z / ntv, blockIdx.x, blockIdx.z % ntv, buf0,
+                   buf1, sh, ph);
 }
 
 // Persistent launch over the (view, tile) items of several volumes: each CTA takes the next item
@@ -638,7 +642,15 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     const int nx = p.vol.nx, ny = p.vol.ny, nz = p.vol.nz;
-    const int per_launch = 65535 / p.n_views > 0 ? 65535 / p.n_views : 1;
+    // Grid order: tile columns fastest, then views, then tile rows and batch items. The CTAs resident at
+    // one time are then the tiles of one tile row in about ten consecutive views; their rays cross one
+    // band of the volume (the band of z that the row sees, widened by the cone angle), which stays in L2
+    // while it is read. With views outermost the resident CTAs would sweep the whole volume once per view,
+    // from DRAM once the volume exceeds L2. Views beyond the 65535 grid rows and batches beyond 65535
+    // tile rows are split into several launches (tables and sinogram offset by the launch's first view).
+    const int ntv = ceil_div(p.det.nv, TMA_TV);
+    const int per_launch = 65535 / ntv > 0 ? 65535 / ntv : 1;
+    const long long view_elems = (long long)p.det.nv * p.det.nu;
     for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
         const int nb = p.batch - b0 < per_launch ? p.batch - b0 : per_launch;
         const T *vptr = (const T *)vol + b0 * p.vol_elems;
@@ -652,8 +664,16 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
         std::memset(&maps, 0, sizeof(maps));
         const int rc = encode_maps<T>(p, cfg, vptr, tptr, nb, maps.map);
         if (rc) return rc;
-        dim3 grid(ceil_div(p.det.nu, TMA_TU), ceil_div(p.det.nv, TMA_TV), p.n_views * nb);
-        kern<<<grid, TMA_NT, smem, st>>>(p, cfg, maps, vptr, (T *)sino + b0 * p.sino_elems);
+        for (int v0 = 0; v0 < p.n_views; v0 += 65535) {
+            const int nvw = p.n_views - v0 < 65535 ? p.n_views - v0 : 65535;
+            OpParams q = p;
+            q.fp = p.fp + v0;
+            q.bp = p.bp ? p.bp + v0 : nullptr;
+            q.views64 = p.views64 ? p.views64 + (size_t)v0 * VIEW64_STRIDE : nullptr;
+            q.n_views = nvw;
+            dim3 grid(ceil_div(p.det.nu, TMA_TU), nvw, ntv * nb);
+            kern<<<grid, TMA_NT, smem, st>>>(q, cfg, maps, vptr, (T *)sino + b0 * p.sino_elems + v0 * view_elems);
+        }
     }
     return (int)cudaGetLastError();
 }

@@ -18,7 +18,7 @@ __global__ void axpy_kernel(T *__restrict__ vol, const T *__restrict__ w, float 
     for (; i < n; i += stride) vol[i] = from_f32<T>(fmaf(alpha, to_f32<T>(w[i]), to_f32<T>(vol[i])));
 }
 
-static int blocks_for(long long n) { return (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16); }
+static int blocks_for(long long n) { return stride_grid(n, 16); }
 
 int launch_residual(const void *a, const void *b, void *out, long long n, int dtype, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;

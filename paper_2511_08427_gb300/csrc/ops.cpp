@@ -132,7 +132,11 @@ int pyronn_fp(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch
         std::lock_guard<std::mutex> lk(g->mu);
         return cuda_rc(launch_fp_tex(g, p, vol, sino, stream), "forward projection launch");
     }
-    if (g->fp_variant == 0 || g->fp_variant == 3 || g->fp_variant == 4) {
+    if (g->fp_variant == 5 && fp_texf_usable(g, dtype)) {
+        std::lock_guard<std::mutex> lk(g->mu);
+        return cuda_rc(launch_fp_texf(g, p, vol, sino, dtype, stream), "forward projection launch");
+    }
+    if (g->fp_variant == 0 || g->fp_variant >= 3) {
         const FpTmaBox &tb = tma_cfg(g, dtype);
         if (tb.depth > 0) {
             if (tb.xt) {
@@ -155,7 +159,8 @@ int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out) {
     int kernel = 1;
     if (g->fp_variant == 1) kernel = 1;
     else if (g->fp_variant == 4 && fp_tex_usable(g, 1, dtype)) kernel = 4;
-    else if ((g->fp_variant == 0 || g->fp_variant == 3 || g->fp_variant == 4) && tb.depth > 0) kernel = 3;
+    else if (g->fp_variant == 5 && fp_texf_usable(g, dtype)) kernel = 5;
+    else if ((g->fp_variant == 0 || g->fp_variant >= 3) && tb.depth > 0) kernel = 3;
     else if (sc.valid) kernel = 2;
     out[0] = kernel;
     out[1] = kernel == 3 ? tb.depth : sc.depth;
@@ -222,6 +227,22 @@ int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
             g->tuning.adj_accum = value;
             g->adj_cfg_ready = 0;
             break;
+        case PYRONN_TUNE_ADJ_DEPTH:
+            if (value != 0 && (value < 2 || value > 16))
+                return set_error(PYRONN_INVALID_ARG, "adjoint slab depth must be 0 (automatic) or in [2, 16] (got %d)", value);
+            g->tuning.adj_depth = value;
+            g->adj_cfg_ready = 0;
+            break;
+        case PYRONN_TUNE_ADJ_LANES:
+            if (value < 0 || value > 2) return set_error(PYRONN_INVALID_ARG, "lane mapping %d out of [0, 2]", value);
+            g->tuning.adj_lanes = value;
+            g->adj_cfg_ready = 0;
+            break;
+        case PYRONN_TUNE_BP_BRICK_Z:
+            if (value != 0 && value != 4 && value != 8 && value != 16)
+                return set_error(PYRONN_INVALID_ARG, "brick depth must be 0 (automatic), 4, 8 or 16 (got %d)", value);
+            g->tuning.bp_brick_z = value;
+            break;
         default:
             return set_error(PYRONN_INVALID_ARG, "unknown tuning parameter %d", param);
     }
@@ -233,7 +254,7 @@ int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
     if (op < 0 || op > 2) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
-    const int vmax = op == 0 ? 4 : (op == 1 ? 3 : 2);
+    const int vmax = op == 0 ? 5 : (op == 1 ? 3 : 2);
     if (variant < 0 || variant > vmax) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
     if (op == 0) g->fp_variant = variant;
     else if (op == 1) g->adj_variant = variant;
@@ -396,7 +417,7 @@ int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch
     OpParams p = make_params(g, batch);
     p.weight = weight;
     if (g->bp_variant == 1) return cuda_rc(launch_bp(p, sino, vol, dtype, stream), "back-projection launch");
-    return cuda_rc(launch_bp_brick(p, sino, vol, dtype, stream), "back-projection launch");
+    return cuda_rc(launch_bp_brick(p, g->tuning.bp_brick_z, sino, vol, dtype, stream), "back-projection launch");
 }
 
 int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, int weight,

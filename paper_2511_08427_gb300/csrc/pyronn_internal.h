@@ -115,6 +115,7 @@ struct AdjSlabCfg {
     int allow_fixed;           // int32 fixed-point boxes where the per-slab bound allows
     int cell_fixed;            // fixed-point boxes: 1 cell-accumulated reductions, 0 one per sample
     int xpad;                  // x-march boxes get an odd row pitch (one word more than the x extent)
+    int lanes;                 // lane-to-pixel mapping: 0 lanes along a tile row, 1 every other pixel of two rows
 };
 
 // Batched (persistent) launches: per-volume descriptions of one plan, in processing order.
@@ -147,6 +148,9 @@ struct Tuning {
     int adj_accum = 0;         // slab adjoint boxes: 0 automatic, 1 FP32 only, 2 fixed point with cells
     int fp_transpose = 0;      // TMA forward projector, x-march tiles: 0 y-fastest copy where usable, 1 never
     int adj_pitch = 0;         // slab adjoint, x-march boxes: 0 odd row pitch where it fits, 1 16-byte pitch
+    int adj_depth = 0;         // slab adjoint: slab depth (0 automatic: the deepest that fits two CTAs per SM)
+    int bp_brick_z = 0;        // brick back-projector: voxels per thread along z (0 automatic = 8; 4, 8 or 16)
+    int adj_lanes = 0;         // slab adjoint lane-to-pixel mapping (0 automatic, 1 tile rows, 2 interleaved)
 };
 
 }  // namespace pyronn
@@ -183,6 +187,9 @@ struct pyronn_geom {
     unsigned long long tex_obj = 0;    // its texture object
     void *d_tex_org = nullptr;     // tile origins (float2 per tile)
     int tex_batch = 0;             // volumes the array holds
+    void *texf_arr = nullptr;      // 3D array of the hardware-filtered texture projector (cudaArray_t)
+    unsigned long long texf_obj = 0;   // its texture object (linear filtering, border addressing)
+    int texf_dtype = -1;           // element type the array holds
     void *d_upd_sino = nullptr;    // work buffers of pyronn_adjoint_update on the unfused kernels
     void *d_upd_vol = nullptr;
     void *d_vol_t = nullptr;           // y-fastest copy of the volume for the TMA forward projector
@@ -200,7 +207,8 @@ struct pyronn_geom {
     pyronn::FpTmaBox tma_cfg[3] = {};   // per dtype
     pyronn::Tuning tuning;
     int tma_ready[3] = {0, 0, 0};
-    int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged (thread loads), 3 slab-staged (TMA), 4 texture gather
+    int fp_variant = 0;            // 0 auto, 1 direct, 2 slab-staged (thread loads), 3 slab-staged (TMA), 4 texture
+                                   // gather, 5 hardware-filtered texture (approximate weights, opt-in)
     int adj_variant = 0;           // 0 auto, 1 atomic scatter, 2 output-stationary bricks, 3 slab-ordered
     pyronn::AdjSlabCfg adj_cfg{};
     int adj_cfg_ready = 0;
@@ -239,6 +247,8 @@ int launch_sim_ring(const void *in, void *out, const int *cols, const float *gai
 int launch_sim_blur(const void *in, void *out, const float *angles, int length, int nu, int nv, int n_views, long long n,
                     int dtype, void *stream);
 int launch_fp_tex(pyronn_geom *g, const OpParams &p, const void *vol, void *sino, void *stream);
+bool fp_texf_usable(const pyronn_geom *g, int dtype);
+int launch_fp_texf(pyronn_geom *g, const OpParams &p, const void *vol, void *sino, int dtype, void *stream);
 int launch_axpy(void *vol, const void *w, float alpha, long long n, int dtype, void *stream);
 int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);
 int adjoint_slab_batched_occupancy(size_t smem, int *blocks_per_sm);
@@ -261,10 +271,15 @@ int launch_adjoint_slab(const OpParams &p, const AdjSlabCfg &c, const void *sino
                         bool accumulate, void *vol, float *acc32, int dtype, void *stream);
 int launch_adjoint_scatter_acc(const OpParams &p, const void *sino, float *acc, void *vol, int dtype, void *stream);
 int launch_bp(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
-int launch_bp_brick(const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
+// bz: voxels per thread along z for 3D volumes (4, 8 or 16; 0 = 8)
+int launch_bp_brick(const OpParams &p, int bz, const void *sino, void *vol, int dtype, void *stream);
 int launch_bp_transpose(const OpParams &p, const void *vol, void *sino, float *acc32, int dtype, void *stream);
 
 size_t dtype_size(int dtype);
+
+// Grid size of a grid-stride element-wise kernel of 256 threads over n elements: enough CTAs for n, at
+// most ctas_per_sm per SM of the current device (its SM count is queried once per device).
+int stride_grid(long long n, int ctas_per_sm);
 
 // Box extent (voxels) covering a span of index coordinates plus a margin, at most cap; -1 where the
 // span is not finite (a corner ray parallel to the slab planes), which bounds nothing: the kernels

@@ -23,7 +23,8 @@ from ._lib import BF16, BP_INV_W2, BP_PLAIN, F16, F32, DetDesc, VolDesc, check, 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 # tuning parameters of Geometry.set_tuning (pyronn_tuning_param)
-TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM, TUNE_FP_CTAS_PER_SM, TUNE_FP_TRANSPOSE, TUNE_ADJ_PITCH = 0, 1, 2, 3, 4, 5
+(TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM, TUNE_FP_CTAS_PER_SM, TUNE_FP_TRANSPOSE, TUNE_ADJ_PITCH, TUNE_ADJ_DEPTH,
+ TUNE_BP_BRICK_Z, TUNE_ADJ_LANES) = 0, 1, 2, 3, 4, 5, 6, 7, 8
 
 
 def _dp(a: np.ndarray):
@@ -458,29 +459,36 @@ class GradientStepFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, p, alpha, g):
         pm = forward_project(x.contiguous(), g)
+        # the fused kernel takes the step as a host scalar: a Python float or a CPU tensor costs nothing, a
+        # CUDA tensor is read back once here (the backward reuses this value)
         a = float(alpha)
         out = adjoint_update(x.detach().clone(memory_format=torch.contiguous_format), pm, g, -a, sino_b=p)
         ctx.g = g
         ctx.alpha = a
-        ctx.save_for_backward(pm, p, alpha)
+        ctx.alpha_is_tensor = isinstance(alpha, torch.Tensor)
+        ctx.alpha_like = alpha if ctx.alpha_is_tensor else None
+        ctx.save_for_backward(pm, p)
         return out
 
     @staticmethod
     def backward(ctx, grad):
-        pm, p, alpha = ctx.saved_tensors
+        pm, p = ctx.saved_tensors
         g, a = ctx.g, ctx.alpha
         grad = grad.contiguous()
         ag = forward_project(grad, g)
         gx = adjoint_update(grad.clone(), ag, g, -a) if ctx.needs_input_grad[0] else None
         gp = a * ag if ctx.needs_input_grad[1] else None
         galpha = None
-        if ctx.needs_input_grad[2]:
-            galpha = (-torch.sum(ag * (pm - p), dtype=torch.float64)).to(alpha.dtype).reshape(alpha.shape)
+        if ctx.needs_input_grad[2] and ctx.alpha_is_tensor:
+            al = ctx.alpha_like
+            galpha = (-torch.sum(ag * (pm - p), dtype=torch.float64)).to(al.dtype).reshape(al.shape)
         return gx, gp, galpha, None
 
 
 def gradient_step(x, p, alpha, g):
-    """x - alpha A^T (A x - p) (fused update, differentiable in x, p and alpha)."""
+    """x - alpha A^T (A x - p) (fused update, differentiable in x, p and alpha). alpha: a Python float, or a
+    tensor of one element (a gradient reaches it when it requires one); a CUDA tensor is read back once per
+    call, since the fused kernel takes the step as a scalar argument."""
     return GradientStepFn.apply(x, p, alpha, g)
 
 

@@ -285,6 +285,33 @@ def test_argument_checks_precede_the_device(L):
     assert L.pyronn_sim_ring(h, a, b, a, a, 1, 2, 9, 0, 1, None) == -1    # views [2, 9) of 3
     assert L.pyronn_sim_gaussian_noise(h, a, b, None, 0.0, 1.0, 0, 1, None) == -1
     assert L.pyronn_fp(h, ctypes.c_void_p(8), b, 0, 1, None) == -3        # misaligned
+    res = (ctypes.c_double * 4)()
+    assert L.pyronn_autotune(h, 3, a, b, 0, 2, None, res) == -1          # unknown operator
+    assert L.pyronn_autotune(h, 0, a, b, 0, 0, None, res) == -1          # no timed launch
+    assert L.pyronn_autotune(h, 1, a, b, 5, 2, None, res) == -2          # unknown element type
+    assert L.pyronn_autotune(h, 2, None, b, 0, 2, None, res) == -1       # null buffer
+    assert L.pyronn_autotune(h, 2, a, b, 0, 2, None, None) == -1         # null result
+
+
+def test_tuning_knobs_of_the_autotuner(L):
+    """The knobs pyronn_autotune sets: an adjoint slab depth is taken as given (two CTAs per SM where its
+    box fits, one otherwise), 0 restores the automatic choice, and out-of-range values are refused."""
+    from paper_2511_08427_gb300 import PyronnError
+    from paper_2511_08427_gb300.operators import TUNE_ADJ_DEPTH, TUNE_BP_BRICK_Z, Geometry
+    g = Geometry.cone_circular((64, 96, 128), (0.5, 0.5, 0.5), (100, 130), (0.6, 0.6), 40, 2 * math.pi, 750.0, 1200.0)
+    auto = g.adjoint_config()
+    for d in (3, 4, 5, 6, 8):
+        g.set_tuning(TUNE_ADJ_DEPTH, d)
+        c = g.adjoint_config()
+        assert c["kernel"] == 3 and c["depth"] == d
+        assert c["max_slabs"] == (128 + 2 + d - 1) // d
+    g.set_tuning(TUNE_ADJ_DEPTH, 0)
+    assert g.adjoint_config() == auto
+    for knob, bad in ((TUNE_ADJ_DEPTH, 1), (TUNE_ADJ_DEPTH, 17), (TUNE_BP_BRICK_Z, 5), (TUNE_BP_BRICK_Z, 32)):
+        with pytest.raises(PyronnError):
+            g.set_tuning(knob, bad)
+    for bz in (0, 4, 8, 16):
+        g.set_tuning(TUNE_BP_BRICK_Z, bz)
 
 
 def test_caller_tensors_are_checked_before_the_library_sees_them(L):

@@ -109,6 +109,12 @@ def test_gradient_step_and_layers_route_through_the_abi(rec):
     assert x.grad.shape == x.shape and p.grad.shape == p.shape and alpha.grad.shape == alpha.shape
     names = [c[0] for c in rec.calls]
     assert names.count("pyronn_fp") == 2 and names.count("pyronn_adjoint_update") == 2
+    # a plain Python step: no gradient for it, the others as before
+    x2 = torch.zeros(4, 6, 8, requires_grad=True)
+    ops.gradient_step(x2, p, 0.1, g).sum().backward()
+    assert x2.grad.shape == x2.shape
+    names = [c[0] for c in rec.calls]
+    assert names.count("pyronn_fp") == 4 and names.count("pyronn_adjoint_update") == 4
     q = ops.ConeProjectionFor3D()(torch.zeros(4, 6, 8), g)
     assert q.shape == (3, 5, 7)
     bq = ops.ConeBackProjectionFor3D()(q, g)

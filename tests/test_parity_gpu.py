@@ -498,12 +498,11 @@ def test_many_views_times_batch_splits_launches(ops):
 
 
 def test_many_views_times_batch_splits_tma_launches(ops):
-    """3D: V * B above the 65535 grid rows, so the TMA projector's launcher splits the batch (21 + 4
-    volumes) and makes the y-fastest copies per part; every volume equals its single projection. The
-    slab adjoint's split batch and its single calls each match the oracle at the FP32 parity bound:
-    they are not compared with each other bit for bit, because the boxes reach the volume through
-    FP32 global reductions whose order depends on scheduling (each result carries its own rounding,
-    about 1e-6 relative on a Gaussian cotangent over 3000 views)."""
+    """3D, 3000 views x 25 volumes: the TMA projector makes the y-fastest copies of the whole batch and
+    every volume equals its single projection; the slab adjoint's batched and single calls each match
+    the oracle at the FP32 parity bound. They are not compared with each other bit for bit, because the
+    boxes reach the volume through FP32 global reductions whose order depends on scheduling (each result
+    carries its own rounding, about 1e-6 relative on a Gaussian cotangent over 3000 views)."""
     from paper_2511_08427_gb300.operators import Geometry
     V, B = 3000, 25
     g = Geometry.cone_circular((8, 8, 8), (1.0, 1.0, 1.0), (4, 4), (1.0, 1.0), V, 2 * math.pi, 30.0, 50.0)
@@ -519,6 +518,44 @@ def test_many_views_times_batch_splits_tma_launches(ops):
         want = oracle.adjoint(og, host(y[i]))
         assert rel_l2(host(a[i]), want) <= 1e-5, i
         assert rel_l2(host(ops.adjoint(y[i].contiguous(), g)), want) <= 1e-5, i
+
+
+def test_more_views_than_grid_rows_split_launches(ops):
+    """70000 views (more than the 65535 grid rows the slab kernels put views on): the TMA projector and
+    the slab adjoint split the views into launches whose tables and sinogram start at the launch's first
+    view; both match the oracle."""
+    from paper_2511_08427_gb300.operators import Geometry
+    V = 70000
+    args = ((8, 8, 8), (1.0, 1.0, 1.0), (4, 4), (1.0, 1.0), V, 2 * math.pi, 30.0, 50.0)
+    g = Geometry.cone_circular(*args)
+    og = oracle.cone_circular(*args)
+    assert g.fp_config()["kernel"] == 3 and g.adjoint_config()["kernel"] == 3
+    x = inputs.uniform((8, 8, 8), seed=31)
+    p = host(ops.forward_project(to_dev(x), g))
+    assert rel_l2(p, oracle.fp(og, x)) <= 1e-5
+    y = inputs.gaussian(og.sino_shape, seed=32)
+    assert rel_l2(host(ops.adjoint(to_dev(y), g)), oracle.adjoint(og, y)) <= 1e-5
+    assert g.read_flags()[:4] == [0, 0, 0, 0]
+
+
+def test_batch_times_tile_rows_split_launches(ops):
+    """One view on a 2048-row detector (128 tile rows of the projector, 64 of the adjoint) and 1100
+    volumes: tile rows x batch items exceed the 65535 grid layers, so both kernels split the batch;
+    every volume's projection equals its single projection and the adjoints match the oracle."""
+    from paper_2511_08427_gb300.operators import Geometry
+    B = 1100
+    args = ((8, 8, 8), (1.0, 1.0, 1.0), (2048, 8), (0.01, 2.0), 1, 2 * math.pi, 30.0, 50.0)
+    g = Geometry.cone_circular(*args)
+    og = oracle.cone_circular(*args)
+    assert g.fp_config()["kernel"] == 3 and g.adjoint_config()["kernel"] == 3
+    x = torch.rand((B, 8, 8, 8), device=DEV, generator=torch.Generator(device=DEV).manual_seed(4))
+    p = ops.forward_project(x, g)
+    y = torch.randn_like(p)
+    a = ops.adjoint(y, g)
+    for i in (0, 510, 511, 1022, 1023, 1099):
+        assert torch.equal(p[i], ops.forward_project(x[i].contiguous(), g)), i
+        assert rel_l2(host(p[i]), oracle.fp(og, host(x[i]))) <= 1e-5, i
+        assert rel_l2(host(a[i]), oracle.adjoint(og, host(y[i]))) <= 1e-5, i
 
 
 def test_misaligned_pointer_is_rejected(ops):
