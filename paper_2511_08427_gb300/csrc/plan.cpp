@@ -62,6 +62,7 @@ int pyronn_plan_create(int n, const pyronn_geom_t *geoms, int dtype, pyronn_plan
             // forward projection runs them through the per-geometry projector on the same stream
             FpTmaBox c = choose_fp_tma_box(g, dtype_size(dtype), g->tuning.fp_depth, g->tuning.fp_nbuf,
                                            g->tuning.fp_minb, g->tuning.fp_transpose == 0);
+            c.packed = g->tuning.fp_packed == 1 ? 0 : (g->tuning.fp_packed == 2 ? 1 : 2);
             P->geoms.push_back(g);
             P->cfg.push_back(c);
         }

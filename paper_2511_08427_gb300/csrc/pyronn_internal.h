@@ -104,6 +104,7 @@ struct FpTmaBox {
     int nbuf;                  // 1 or 2 shared-memory buffers
     int minb;                  // CTAs per SM the single-volume kernel is compiled for (2 or 4)
     int xt;                    // x-march boxes come from a y-fastest copy of the volume (y innermost)
+    int packed;                // sample loop: 0 scalar, 1 packed FP32x2 lerps, 2 packed lerps and (x, y) positions
 };
 
 // Slab-ordered adjoint configuration (chosen per geometry).
@@ -151,6 +152,7 @@ struct Tuning {
     int adj_depth = 0;         // slab adjoint: slab depth (0 automatic: the deepest that fits two CTAs per SM)
     int bp_brick_z = 0;        // brick back-projector: voxels per thread along z (0 automatic = 8; 4, 8 or 16)
     int adj_lanes = 0;         // slab adjoint lane-to-pixel mapping (0 automatic, 1 tile rows, 2 interleaved)
+    int fp_packed = 0;         // TMA forward projector: 0 automatic (= 3), 1 scalar, 2 packed lerps, 3 packed lerps and positions
 };
 
 }  // namespace pyronn

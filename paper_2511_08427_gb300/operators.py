@@ -24,7 +24,7 @@ _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
 
 # tuning parameters of Geometry.set_tuning (pyronn_tuning_param)
 (TUNE_FP_DEPTH, TUNE_FP_BUFFERS, TUNE_ADJ_ACCUM, TUNE_FP_CTAS_PER_SM, TUNE_FP_TRANSPOSE, TUNE_ADJ_PITCH, TUNE_ADJ_DEPTH,
- TUNE_BP_BRICK_Z, TUNE_ADJ_LANES) = 0, 1, 2, 3, 4, 5, 6, 7, 8
+ TUNE_BP_BRICK_Z, TUNE_ADJ_LANES, TUNE_FP_PACKED) = 0, 1, 2, 3, 4, 5, 6, 7, 8, 9
 
 
 def _dp(a: np.ndarray):

@@ -68,13 +68,15 @@ def test_autotune_applies_its_choice_and_keeps_the_operator(ops, op, tmp_path, m
     _check_operator(ops, g2, og, op)
 
 
+@pytest.mark.parametrize("lanes", [1, 2])
 @pytest.mark.parametrize("depth", [3, 4, 5, 6, 8])
-@pytest.mark.parametrize("name", ["cone_tma_rows", "jittered_positions"])
-def test_adjoint_slab_depths_match_the_oracle(ops, name, depth):
+@pytest.mark.parametrize("name", ["cone_tma_rows", "jittered_positions", "cone_aniso_offset"])
+def test_adjoint_slab_depths_match_the_oracle(ops, name, depth, lanes):
     case = next(c for c in SMALL if c.name == name)
     g = case.library_geometry()
     og = case.oracle_geometry()
     g.set_tuning(ops.TUNE_ADJ_DEPTH, depth)
+    g.set_tuning(ops.TUNE_ADJ_LANES, lanes)
     c = g.adjoint_config()
     assert c["kernel"] == 3 and c["depth"] == depth
     y = inputs.gaussian(og.sino_shape, seed=83)

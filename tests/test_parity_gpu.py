@@ -184,6 +184,34 @@ def test_slab_adjoint_spiky_sinogram(ops):
     assert rel_l2(small, oracle.adjoint(og, base)) <= 5e-3
 
 
+def test_slab_adjoint_high_dynamic_range_cotangent(ops):
+    """Cotangent magnitudes spread log-uniformly over four decades inside every detector tile, signs
+    random. The fixed-point boxes round each contribution to a quantum of at most 2^-21 of the tile's
+    largest |y| dt, so the error of a voxel is bounded by that quantum times the number of contributions
+    it receives, not by its own value: voxels reached only by small cotangent values carry a larger
+    relative error than the FP32 path would give them. The test holds the whole result to the FP32
+    parity bound and every voxel to 1e-5 of the largest value, and prints the relative error of the
+    voxels whose values are below 1e-3 of the largest (the trade-off the fixed-point boxes make)."""
+    case = [c for c in SMALL3 if c.name.startswith("cone")][0]
+    g = case.library_geometry()
+    g.set_variant(1, 3)
+    og = case.oracle_geometry()
+    rng = np.random.default_rng(26)
+    mag = 10.0 ** rng.uniform(-4.0, 0.0, size=og.sino_shape)
+    y = (mag * rng.choice([-1.0, 1.0], size=og.sino_shape)).astype(np.float32)
+    a = host(ops.adjoint(to_dev(y), g))
+    ref = oracle.adjoint(og, y)
+    assert rel_l2(a, ref) <= 1e-5
+    err = np.abs(a - ref)
+    top = np.abs(ref).max()
+    assert err.max() <= 1e-5 * top
+    small = (np.abs(ref) < 1e-3 * top) & (np.abs(ref) > 0)
+    if small.any():
+        print(f"high-dynamic-range cotangent: rel-L2 {rel_l2(a, ref):.2e}; voxels below 1e-3 of the maximum: "
+              f"rel-L2 {rel_l2(a[small], ref[small]):.2e}, max error / max value {err.max() / top:.2e}")
+    assert g.read_flags()[4] > 0   # the slabs did accumulate in fixed point
+
+
 @pytest.mark.parametrize("pitch", [0, 1])
 @pytest.mark.parametrize("case", SMALL3, ids=lambda c: c.name)
 def test_slab_adjoint_box_pitch(ops, case, pitch):
@@ -697,3 +725,19 @@ def test_variants_agree_at_full_size(ops):
         p2 = ops.forward_project(x, g)
         assert rel_l2(host(p2), host(p1)) <= 2e-6
         assert g.read_flags()[:4] == [0, 0, 0, 0]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("case", [c for c in SMALL if c.ndim == 3], ids=lambda c: c.name)
+def test_packed_interpolation_is_bit_identical(ops, case, dtype):
+    """The TMA projector's packed FP32x2 arithmetic (lerps: the default; lerps and positions) and its
+    scalar form round every lane the same way, so the projections are identical bit for bit."""
+    g = case.library_geometry()
+    if g.fp_config(dtype)["kernel"] != 3:
+        pytest.skip("the TMA-staged projector does not apply to this geometry")
+    x = to_dev(case.phantom(), dtype)
+    g.set_tuning(ops.TUNE_FP_PACKED, 1)
+    scalar = ops.forward_project(x, g)
+    for mode in (2, 3):
+        g.set_tuning(ops.TUNE_FP_PACKED, mode)
+        assert torch.equal(ops.forward_project(x, g), scalar), mode
