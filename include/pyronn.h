@@ -344,7 +344,9 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * the rays of a warp, which spread across y there, read consecutive shared-memory words; 1 stages
  * every slab from the volume itself; PYRONN_TUNE_ADJ_PITCH: 0 (automatic) gives the slab-ordered
  * adjoint's x-march boxes an odd row pitch (one word more than their x extent) wherever a slab depth
- * still fits two CTAs per SM with it, 1 keeps rows of whole 16-byte groups; PYRONN_TUNE_ADJ_DEPTH: slab
+ * still fits two CTAs per SM with it, and its y- and z-march boxes a row pitch that is a multiple of 32
+ * words wherever the padded box fits its capacity; 1 keeps rows of whole 16-byte groups everywhere; 2 as
+ * 0 without the 32-word pitch; PYRONN_TUNE_ADJ_DEPTH: slab
  * depth of the slab-ordered adjoint in voxel planes, 2 .. 16 (0 automatic: the deepest of 8, 6, 5, 4 whose
  * box lets two CTAs share an SM; a depth whose box does not fit runs one CTA per SM, or the brick adjoint
  * if the box exceeds 160 KB); PYRONN_TUNE_BP_BRICK_Z: voxels per thread along z of the brick
@@ -411,7 +413,7 @@ PYRONN_API int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out);
 /* Matched-adjoint configuration (host computation, no GPU needed), 8 ints: [0] kernel (1 atomic
  * scatter, 2 bricks, 3 slab-ordered), [1] slab depth, [2] guard planes, [3] shared-memory box
  * capacity in floats, [4] 1 if x-march boxes have an odd row pitch, [5] slab-table capacity,
- * [6..7] zero. */
+ * [6] 1 if y- and z-march boxes get a 32-word row pitch where it fits, [7] zero. */
 PYRONN_API int pyronn_geom_adjoint_config(pyronn_geom_t g, int *out);
 
 /* Message describing the last error of the calling thread ("" if none). */

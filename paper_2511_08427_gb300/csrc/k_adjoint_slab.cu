@@ -498,7 +498,14 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         // x-march tiles: the lanes of a warp sit on different rows at nearly the same x, so the rows get
         // an odd pitch (where the configuration's box budget allows), which puts 32 consecutive rows on
         // 32 different banks
-        const int px = m == 0 && cfg.xpad ? e0 + 1 : e0;
+        // y- and z-march tiles: the lanes of a warp sit along x, so a row pitch that is a multiple of 32
+        // words puts every voxel of a column (same x) on one bank whatever its row or plane; neighbouring
+        // rays then collide only when they share a cell (where the padded box still fits the capacity)
+        int px = m == 0 && cfg.xpad ? e0 + 1 : e0;
+        if (m != 0 && cfg.ypad) {
+            const int p32 = (e0 + 31) & ~31;
+            if ((long long)p32 * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) <= box_cap) px = p32;
+        }
         const int e1 = hi[1] - lo[1] + 1, e2 = hi[2] - lo[2] + 1;
         const bool fits = e0 > 0 && e1 > 0 && e2 > 0 && (long long)px * e1 * e2 <= box_cap;
         for (int a = 0; a < 3; ++a) S.lo[a] = lo[a];
@@ -954,7 +961,7 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     const int forced = g->tuning.adj_depth;
     const int depths[4] = {8, 6, 5, 4};
     const int ndepths = forced > 0 ? 1 : 4;
-    for (int xpad = g->tuning.adj_pitch == 1 ? 0 : 1; xpad >= 0 && !fit; --xpad)
+    for (int xpad = g->tuning.adj_pitch == 1 ? 0 : 1; xpad >= 0 && !fit; --xpad)   // 0 and 2: odd x-march pitch
         for (int di = 0; di < ndepths; ++di) {
             const int depth = forced > 0 ? forced : depths[di];
             need = as_bound(g, depth, c.guard, xpad);
@@ -972,6 +979,7 @@ AdjSlabCfg choose_adj_slab_cfg(const pyronn_geom *g) {
     c.allow_fixed = g->tuning.adj_accum != 1;
     c.cell_fixed = g->tuning.adj_accum == 2;
     c.lanes = g->tuning.adj_lanes == 2 ? 1 : 0;
+    c.ypad = g->tuning.adj_pitch == 0;
     return c;
 }
 

@@ -193,6 +193,7 @@ int pyronn_geom_adjoint_config(pyronn_geom_t g, int *out) {
     out[3] = ac.box_cap;
     out[4] = ac.xpad;
     out[5] = ac.max_slabs;
+    out[6] = ac.ypad;
     return PYRONN_OK;
 }
 
@@ -215,7 +216,7 @@ int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
             g->tuning.fp_minb = value;
             break;
         case PYRONN_TUNE_ADJ_PITCH:
-            if (value < 0 || value > 1) return set_error(PYRONN_INVALID_ARG, "pitch mode %d out of [0, 1]", value);
+            if (value < 0 || value > 2) return set_error(PYRONN_INVALID_ARG, "pitch mode %d out of [0, 2]", value);
             g->tuning.adj_pitch = value;
             g->adj_cfg_ready = 0;
             break;

@@ -117,6 +117,7 @@ struct AdjSlabCfg {
     int cell_fixed;            // fixed-point boxes: 1 cell-accumulated reductions, 0 one per sample
     int xpad;                  // x-march boxes get an odd row pitch (one word more than the x extent)
     int lanes;                 // lane-to-pixel mapping: 0 lanes along a tile row, 1 every other pixel of two rows
+    int ypad;                  // y- and z-march boxes get a row pitch that is a multiple of 32 words where it fits
 };
 
 // Batched (persistent) launches: per-volume descriptions of one plan, in processing order.

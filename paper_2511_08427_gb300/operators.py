@@ -179,7 +179,7 @@ class Geometry:
         out = (ctypes.c_int * 8)()
         check(lib().pyronn_geom_adjoint_config(self._h, out))
         return {"kernel": out[0], "depth": out[1], "guard": out[2], "box_floats": out[3], "odd_pitch": bool(out[4]),
-                "max_slabs": out[5]}
+                "max_slabs": out[5], "pitch32": bool(out[6])}
 
     def set_tuning(self, param: int, value: int) -> None:
         check(lib().pyronn_geom_set_tuning(self._h, int(param), int(value)))

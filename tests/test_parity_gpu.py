@@ -212,15 +212,16 @@ def test_slab_adjoint_high_dynamic_range_cotangent(ops):
     assert g.read_flags()[4] > 0   # the slabs did accumulate in fixed point
 
 
-@pytest.mark.parametrize("pitch", [0, 1])
+@pytest.mark.parametrize("pitch", [0, 1, 2])
 @pytest.mark.parametrize("case", SMALL3, ids=lambda c: c.name)
 def test_slab_adjoint_box_pitch(ops, case, pitch):
-    """x-march boxes with the odd row pitch (0, automatic) and with rows of whole 16-byte groups (1):
-    both match the oracle."""
+    """Box row pitches: 0 (automatic: odd x-march pitch, 32-word y- and z-march pitch where it fits), 1
+    (rows of whole 16-byte groups) and 2 (odd x-march pitch only): all match the oracle."""
     g = case.library_geometry()
     g.set_variant(1, 3)
     g.set_tuning(ops.TUNE_ADJ_PITCH, pitch)
-    assert g.adjoint_config()["odd_pitch"] == (pitch == 0)
+    c = g.adjoint_config()
+    assert c["odd_pitch"] == (pitch != 1) and c["pitch32"] == (pitch == 0)
     og = case.oracle_geometry()
     y = inputs.gaussian(og.sino_shape, seed=26)
     g.read_flags(reset=True)
