@@ -613,16 +613,19 @@ def run_gpu(args):
     big = vol_np.nbytes > 200 * 2 ** 20
     flush = None if big else torch.empty(256 * 1024 * 1024 // 4, device=dev)
 
-    # tile and brick shapes chosen by the library's autotuner on a subset of the views (the per-view work
-    # is the same; the whole geometry would take a minute of timing), applied to the full geometry
+    # tile and brick shapes chosen by the library's autotuner: the projector and the adjoint on an evenly
+    # spaced eighth of the views (the per-view work is the same; the whole geometry would take a minute of
+    # timing), the back-projector on the whole geometry (its staged variant's pipeline start is paid once
+    # per brick, so a subset of the views would understate it; it takes a few seconds)
     from paper_2511_08427_gb300 import autotune
     tuned = {}
     g_sub = make_geometry(name, views=max(1, V // 8))
     for op in ("fp", "adjoint", "bp"):
-        r = autotune.tune(g_sub, op, repeats=2, use_cache=False, device=dev)
+        gt = g if op == "bp" else g_sub
+        r = autotune.tune(gt, op, repeats=2, use_cache=False, device=dev)
         autotune.apply(g, autotune.OPS[op], *r["params"])
-        tuned[op] = {"params": r["params"], "subset_ms": r["ms"], "candidates": r["candidates"],
-                     "subset_views": g_sub.n_views}
+        tuned[op] = {"params": r["params"], "tuned_ms": r["ms"], "candidates": r["candidates"],
+                     "tuned_on_views": gt.n_views}
     del g_sub
     rates = roofline.measure()   # on-chip peaks per SM clock, measured on this GPU before the timed region
     timed_steps(ops, g, vol, sino, cot, adj, bpv, args.warmup, stream, torch, flush)
@@ -711,7 +714,7 @@ def run_gpu(args):
         "rooflines": rl,
         "onchip_peaks": dict(rates, source="roofline_peaks.cu, measured in this run before the timed region"),
         "autotune": dict(tuned, params="fp: (slab depth, buffers); adjoint: (slab depth, pitch mode); bp: (brick "
-                                       "depth, -)"),
+                                       "depth, variant 2 L1 path / 3 staged shadows)"),
         "fp_texture_filtered": texf,
         "hbm": {"compulsory_gb_per_step": (3 * vol_np.nbytes + 3 * V * nv * nu * 4) / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"), "peak_source": peak_src},

@@ -321,8 +321,11 @@ PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void 
  * 2 output-stationary bricks accumulated in shared memory, 3 slab-ordered: detector tiles march
  * the volume like the forward projector, scatter into shared-memory slab boxes and add each box to
  * the volume with vector reductions. op 2 = voxel-driven back-projection: variant 0 automatic
- * (= 2), 1 one thread per voxel in absolute detector coordinates, 2 bricks with detector
- * coordinates relative to the brick centre's projection. All variants compute the same operator,
+ * (= 2; pyronn_autotune picks 3 where it is faster), 1 one thread per voxel in absolute detector
+ * coordinates, 2 bricks with
+ * detector coordinates relative to the brick centre's projection, taps read through L1, 3 the same
+ * bricks with each view's shadow of the brick copied into shared memory by tensor copies, one chunk of
+ * views ahead (3D volumes whose detector rows are a multiple of 16 bytes). All variants compute the same operator,
  * except forward-projection variant 5 (approximate interpolation weights). */
 PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
 
@@ -336,9 +339,9 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * tile's largest |y| dt, FP32 reductions elsewhere; fixed-point boxes take one reduction per sample
  * and corner), 1 FP32 reductions only, 2 as 0 but fixed-point boxes take one reduction per corner of
  * each cell a ray passes (weights summed in registers while the ray stays in the cell);
- * PYRONN_TUNE_FP_CTAS_PER_SM: CTAs per SM the TMA-staged forward projector is compiled for, 2 or
- * 4 (4 caps registers at 64 per thread; automatic: 4 where four CTAs' slab buffers fit in shared
- * memory); PYRONN_TUNE_FP_TRANSPOSE: 0 (automatic) lets the TMA-staged forward projector stage the
+ * PYRONN_TUNE_FP_CTAS_PER_SM: CTAs per SM the TMA-staged forward projector is compiled for, 2, 3 or
+ * 4 (4 caps registers at 64 per thread, 3 at 80; 3 needs three CTAs' slab buffers to fit in shared
+ * memory; automatic: 4 where four CTAs' slab buffers fit); PYRONN_TUNE_FP_TRANSPOSE: 0 (automatic) lets the TMA-staged forward projector stage the
  * slabs of detector tiles that march along x from a y-fastest copy of the volume, made on the
  * call's stream into a geometry-owned buffer of the volume's size (allocated on first use), so that
  * the rays of a warp, which spread across y there, read consecutive shared-memory words; 1 stages
@@ -378,11 +381,11 @@ PYRONN_API int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value);
  * pyronn_geom_set_tuning (the choice stays with g). op 0: forward projection, in = volume, out =
  * sinogram; candidates (slab depth, buffers) of the TMA-staged projector. op 1: matched adjoint,
  * in = sinogram, out = volume; candidates (slab depth, pitch mode) of the slab-ordered adjoint. op 2:
- * voxel-driven back-projection (plain weights), in = sinogram, out = volume; candidates: brick depth
- * 4, 8, 16 (3D). Buffers hold one batch item of dtype (device memory, 16-byte aligned); out is
+ * voxel-driven back-projection (plain weights), in = sinogram, out = volume; candidates (brick depth,
+ * variant): depths 4, 8, 16 of the L1-path bricks (variant 2) and the staged bricks (variant 3; 3D). Buffers hold one batch item of dtype (device memory, 16-byte aligned); out is
  * overwritten, in is only read; nothing is allocated beyond what the operators allocate on first use.
  * repeats: timed launches per candidate (1 .. 1000). result[4]: mean milliseconds per launch of the
- * chosen candidate, its two parameters (op 2: brick depth, 0) and the number of candidates timed.
+ * chosen candidate, its two parameters and the number of candidates timed.
  * Synchronises the stream. PYRONN_INVALID_ARG if no candidate applies (the knobs are then left as
  * they were). */
 PYRONN_API int pyronn_autotune(pyronn_geom_t g, int op, const void *in, void *out, int dtype, int repeats,
@@ -415,6 +418,13 @@ PYRONN_API int pyronn_geom_fp_config(pyronn_geom_t g, int dtype, int *out);
  * capacity in floats, [4] 1 if x-march boxes have an odd row pitch, [5] slab-table capacity,
  * [6] 1 if y- and z-march boxes get a 32-word row pitch where it fits, [7] zero. */
 PYRONN_API int pyronn_geom_adjoint_config(pyronn_geom_t g, int *out);
+
+/* Voxel-driven back-projector configuration for element type dtype (host computation, no GPU needed),
+ * 8 ints: [0] kernel (1 one thread per voxel, 2 bricks through L1, 3 bricks with staged detector shadows),
+ * [1], [2] the staged box per view in pixels (u, v; kernel 3), [3] voxels per thread along z, [4] views
+ * per shared-memory stage (kernel 3), [5] elements between the views' boxes in shared memory (kernel 3;
+ * a multiple of 128 bytes), [6..7] zero. */
+PYRONN_API int pyronn_geom_bp_config(pyronn_geom_t g, int dtype, int *out);
 
 /* Message describing the last error of the calling thread ("" if none). */
 PYRONN_API const char *pyronn_last_error(void);

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("pyronn_geom_read_flags", _c_int, [_vp, ctypes.POINTER(_c_int), _c_int]),
     ("pyronn_geom_fp_config", _c_int, [_vp, _c_int, ctypes.POINTER(_c_int)]),
     ("pyronn_geom_adjoint_config", _c_int, [_vp, ctypes.POINTER(_c_int)]),
+    ("pyronn_geom_bp_config", _c_int, [_vp, _c_int, ctypes.POINTER(_c_int)]),
     ("pyronn_last_error", ctypes.c_char_p, []),
     ("pyronn_version", _c_int, []),
 ]

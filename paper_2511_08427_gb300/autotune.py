@@ -2,7 +2,8 @@
 
 ``tune(g, op)`` lets the library time every candidate configuration of one operator of a geometry
 (forward projection: slab depth x buffers of the TMA-staged projector; matched adjoint: slab depth x
-row pitch of the slab-ordered adjoint; back-projection: brick depth) with CUDA events on the current
+row pitch of the slab-ordered adjoint; back-projection: brick depth of the L1-path bricks, or the bricks
+with staged detector shadows) with CUDA events on the current
 stream and apply the fastest. The choice is cached in a JSON file keyed by the device name, the
 operator and a signature of the geometry (shapes, spacings, views, step, element type), so a later
 process re-applies it through pyronn_geom_set_tuning without timing. Every candidate computes the same
@@ -23,8 +24,8 @@ from .operators import (_DTYPES, TUNE_ADJ_DEPTH, TUNE_ADJ_PITCH, TUNE_BP_BRICK_Z
                         TUNE_FP_DEPTH)
 
 OPS = {"fp": 0, "adjoint": 1, "bp": 2}
-# the two tuning knobs each operator's result sets (the second is unused for the back-projector)
-_KNOBS = {0: (TUNE_FP_DEPTH, TUNE_FP_BUFFERS), 1: (TUNE_ADJ_DEPTH, TUNE_ADJ_PITCH), 2: (TUNE_BP_BRICK_Z, None)}
+# the two settings each operator's result sets (the back-projector's second one is its kernel variant)
+_KNOBS = {0: (TUNE_FP_DEPTH, TUNE_FP_BUFFERS), 1: (TUNE_ADJ_DEPTH, TUNE_ADJ_PITCH), 2: (TUNE_BP_BRICK_Z, "variant")}
 
 
 def _cache_path() -> str:
@@ -61,7 +62,9 @@ def _store(db):
 def apply(g, op: int, a: int, b: int) -> None:
     k1, k2 = _KNOBS[op]
     g.set_tuning(k1, int(a))
-    if k2 is not None:
+    if k2 == "variant":
+        g.set_variant(2, int(b))
+    else:
         g.set_tuning(k2, int(b))
 
 

@@ -12,12 +12,12 @@ using namespace pyronn;
 namespace {
 
 struct Candidate {
-    int a, b;   // op 0: slab depth, buffers; op 1: slab depth, pitch mode; op 2: brick depth, unused
+    int a, b;   // op 0: slab depth, buffers; op 1: slab depth, pitch mode; op 2: brick depth, kernel variant
 };
 
 const Candidate FP_CANDIDATES[] = {{8, 2}, {8, 1}, {4, 2}, {4, 1}, {12, 1}, {16, 1}, {6, 1}};
 const Candidate ADJ_CANDIDATES[] = {{8, 0}, {6, 0}, {5, 0}, {4, 0}, {6, 1}, {4, 1}, {3, 0}};
-const Candidate BP_CANDIDATES[] = {{8, 0}, {4, 0}, {16, 0}};
+const Candidate BP_CANDIDATES[] = {{8, 2}, {4, 2}, {16, 2}, {8, 3}};
 
 int apply(pyronn_geom_t g, int op, const Candidate &c) {
     int rc = PYRONN_OK;
@@ -29,7 +29,8 @@ int apply(pyronn_geom_t g, int op, const Candidate &c) {
         if ((rc = pyronn_geom_set_tuning(g, PYRONN_TUNE_ADJ_DEPTH, c.a))) return rc;
         return pyronn_geom_set_tuning(g, PYRONN_TUNE_ADJ_PITCH, c.b);
     }
-    return pyronn_geom_set_tuning(g, PYRONN_TUNE_BP_BRICK_Z, c.a);
+    if ((rc = pyronn_geom_set_tuning(g, PYRONN_TUNE_BP_BRICK_Z, c.a))) return rc;
+    return pyronn_geom_set_variant(g, 2, c.b);
 }
 
 // Whether the candidate runs on the kernel it tunes (a depth whose boxes do not fit makes the library
@@ -38,7 +39,7 @@ bool applicable(pyronn_geom_t g, int op, int dtype) {
     int cfg[20];
     if (op == 0) return pyronn_geom_fp_config(g, dtype, cfg) == PYRONN_OK && cfg[0] == 3;
     if (op == 1) return pyronn_geom_adjoint_config(g, cfg) == PYRONN_OK && cfg[0] == 3;
-    return g->ndim == 3;
+    return g->ndim == 3 && pyronn_geom_bp_config(g, dtype, cfg) == PYRONN_OK && cfg[0] == g->bp_variant;
 }
 
 int run(pyronn_geom_t g, int op, const void *in, void *out, int dtype, void *stream) {
@@ -63,9 +64,11 @@ extern "C" PYRONN_API int pyronn_autotune(pyronn_geom_t g, int op, const void *i
                                      : (int)(sizeof(BP_CANDIDATES) / sizeof(Candidate)));
     // the knobs as they were: restored if no candidate applies
     Tuning before;
+    int before_bp_variant = 0;
     {
         std::lock_guard<std::mutex> lk(g->mu);
         before = g->tuning;
+        before_bp_variant = g->bp_variant;
     }
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -102,6 +105,7 @@ extern "C" PYRONN_API int pyronn_autotune(pyronn_geom_t g, int op, const void *i
     if (rc != PYRONN_OK || best < 0) {
         std::lock_guard<std::mutex> lk(g->mu);
         g->tuning = before;
+        g->bp_variant = before_bp_variant;
         g->adj_cfg_ready = 0;
         g->tma_ready[0] = g->tma_ready[1] = g->tma_ready[2] = 0;
         if (rc != PYRONN_OK) return rc;

@@ -1,0 +1,413 @@
+// TMA-staged voxel-driven back-projector (same operator as bp_brick_kernel and bp_direct_kernel,
+// Sec. 2.1: each voxel projected onto the detector, the bilinear, zero-padded detector values summed
+// over the views).
+//
+// One CTA owns a 16 x 16 x BZ brick (each thread a z-column of BZ voxels, sums in registers over every
+// view), like the L1-path brick kernel. The difference is where the detector taps come from: for every
+// view, one thread copies the brick's shadow on the detector (a box of bu x bv pixels around the
+// projection of the brick centre, sized on the host for the geometry) into shared memory with one 3D
+// tensor copy, whose zero fill stands for the detector's zero padding. Views go in chunks (up to BT_CHUNK
+// views, as many as let four CTAs share an SM) through two shared-memory stages: while the CTA
+// back-projects one chunk, the next chunk's copies are in
+// flight, so the taps are low-latency shared-memory loads instead of first-touch L1 misses, and need no
+// bounds tests. A warp takes the staged path for a view when every lane's column (whose u and v are
+// monotone along z, so its end voxels bound it) falls inside the box with a margin; other warps, and
+// views whose shadow exceeds the box (the box is sized from a sample of bricks), read through L1 as the
+// brick kernel does. Every copy wait is bounded; a lost copy sets FLAG_TMA_TIMEOUT and the CTA leaves.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <type_traits>
+#include <vector>
+
+#include "bp_common.cuh"
+#include "tma_common.cuh"
+
+namespace pyronn {
+
+constexpr int BT_CHUNK = 4;   // most views per stage (the configuration may use fewer, see cfg.chunk)
+
+struct BpTmaCfg {
+    int bu, bv;    // staged box per view (pixels); bu * element size is a multiple of 16 bytes
+    int stride;    // elements between the views' boxes in shared memory: a tensor copy's destination must
+                   // be 128-byte aligned, so bu * bv rounded up to a multiple of 128 bytes
+    int chunk;     // views per stage (1 .. BT_CHUNK): as many as let four CTAs share an SM
+    int valid;     // 0: the kernel does not apply (rows not a multiple of 16 bytes, box too large)
+};
+
+struct BtStage {
+    BpView v[BT_CHUNK];
+    int ub[BT_CHUNK], vb[BT_CHUNK];   // box origin on the detector (ub a multiple of 16 bytes / element)
+    int staged[BT_CHUNK];             // 1: the view's shadow fits the box and was copied
+};
+
+// Per-view set-up of a stage for views n0 .. n0 + cfg.chunk - 1 (threads 0 .. cfg.chunk - 1).
+template <typename T, int BZ>
+__device__ __forceinline__ void bt_setup(const OpParams &p, const BpTmaCfg &cfg, const double Xb[3], int n0,
+                                         BtStage &S) {
+    const int t = threadIdx.x;
+    if (t >= cfg.chunk) return;
+    const int n = n0 + t;
+    S.staged[t] = 0;
+    S.ub[t] = S.vb[t] = 0;
+    if (n >= p.n_views) {
+        S.v[t].valid = 0;
+        return;
+    }
+    BpView &V = S.v[t];
+    bp_view_setup(p, n, Xb, 0.5 * (BZ - 1), V);
+    if (!V.valid || V.eu < 0) return;
+    constexpr int align = 16 / (int)sizeof(T);
+    const int u_lo = V.U0 - V.eu, u_hi = V.U0 + V.eu;
+    const int ub = u_lo >= 0 ? (u_lo / align) * align : -(((-u_lo) + align - 1) / align) * align;
+    const int vb = V.V0 - V.ev;
+    // the box must hold the taps of every voxel; a box entirely off the detector is all zero and is
+    // copied all the same (the copy fills it)
+    if (u_hi - ub + 1 <= cfg.bu && 2 * V.ev + 1 <= cfg.bv) {
+        S.ub[t] = ub;
+        S.vb[t] = vb;
+        S.staged[t] = 1;
+    }
+}
+
+template <typename T, int BZ, bool W2>
+__global__ void __launch_bounds__(BPB_NT, 4) bp_tma_kernel(OpParams p, BpTmaCfg cfg, const __grid_constant__ CUtensorMap map,
+                                                           const T *__restrict__ sino, T *__restrict__ vol) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ BtStage st[2];
+    __shared__ unsigned long long bar[2];
+    const unsigned raw = smem_u32(smem_raw);
+    T *const stage0 = (T *)(smem_raw + (((raw + 127u) & ~127u) - raw));
+    const int per_view = cfg.stride;                                  // slot of one view (128-byte multiple)
+    const int chunk = cfg.chunk;
+    const unsigned view_bytes = (unsigned)(sizeof(T) * cfg.bu * cfg.bv);   // bytes one copy delivers
+
+    const int nbz = (p.vol.nz + BZ - 1) / BZ;
+    const int bxi = blockIdx.x, byi = blockIdx.y, bzi = blockIdx.z % nbz, b = blockIdx.z / nbz;
+    const int bx0 = bxi * BPB_X, by0 = byi * BPB_Y, bz0 = bzi * BZ;
+    const int tid = threadIdx.x;
+    const int lx = tid % BPB_X, ly = tid / BPB_X;
+    const int i = bx0 + lx, j = by0 + ly;
+    const T *sb = sino + (long long)b * p.sino_elems;
+    const int nu = p.det.nu, nv = p.det.nv;
+    double Xb[3];
+    Xb[0] = (bx0 + 0.5 * (BPB_X - 1) - 0.5 * (p.vol.nx - 1)) * p.sx;
+    Xb[1] = (by0 + 0.5 * (BPB_Y - 1) - 0.5 * (p.vol.ny - 1)) * p.sy;
+    Xb[2] = (bz0 + 0.5 * (BZ - 1) - 0.5 * (p.vol.nz - 1)) * p.sz;
+    const float dx = (float)lx - 0.5f * (BPB_X - 1), dy = (float)ly - 0.5f * (BPB_Y - 1);
+    const float dz0 = -0.5f * (BZ - 1);
+
+    float acc[BZ];
+#pragma unroll
+    for (int z = 0; z < BZ; ++z) acc[z] = 0.0f;
+
+    const unsigned bars[2] = {smem_u32(&bar[0]), smem_u32(&bar[1])};
+    if (tid == 0) {
+        mbar_init(bars[0], 1);
+        mbar_init(bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // thread 0 issues the copies of stage s (its set-up is visible to it after a barrier)
+    auto issue = [&](int n0, int s) {
+        unsigned bytes = 0;
+        for (int c = 0; c < chunk; ++c) bytes += st[s].staged[c] ? view_bytes : 0u;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the stage was last read by threads
+        mbar_expect_tx(bars[s], bytes);
+        for (int c = 0; c < chunk; ++c)
+            if (st[s].staged[c])
+                tma_load_3d(smem_u32(stage0 + (size_t)(s * chunk + c) * per_view), &map, bars[s], st[s].ub[c],
+                            st[s].vb[c], b * p.n_views + n0 + c);
+    };
+
+    const int nchunks = (p.n_views + chunk - 1) / chunk;
+    bt_setup<T, BZ>(p, cfg, Xb, 0, st[0]);
+    __syncthreads();
+    if (tid == 0) issue(0, 0);
+    int lost = -1;   // the chunk whose copy did not arrive
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int s = ch & 1;
+        if (ch + 1 < nchunks) bt_setup<T, BZ>(p, cfg, Xb, (ch + 1) * chunk, st[s ^ 1]);
+        __syncthreads();   // stage s ^ 1's set-up is visible; every thread is done with its previous chunk
+        if (tid == 0 && ch + 1 < nchunks) issue((ch + 1) * chunk, s ^ 1);
+        const bool ok = mbar_wait_bounded(bars[s], (unsigned)(ch >> 1) & 1u);
+        if (!__syncthreads_and(ok)) {
+            lost = ch;
+            break;
+        }
+        const BtStage &S = st[s];
+        for (int c = 0; c < chunk; ++c) {
+            const int n = ch * chunk + c;
+            if (n >= p.n_views) break;
+            const BpView &V = S.v[c];
+            if (!V.valid) continue;
+            if (S.staged[c]) {
+                const T *box = stage0 + (size_t)(s * chunk + c) * per_view;
+                // tap (iu, iv) of the detector is box[(iv - vb) bu + (iu - ub)]; iu = floor(qu) + U0
+                const int du0 = V.U0 - S.ub[c], dv0 = V.V0 - S.vb[c];
+                const float eps = 1e-3f;
+                const float lu = (float)(-du0) + eps, hu = (float)(cfg.bu - 1 - du0) - eps;
+                const float lvv = (float)(-dv0) + eps, hvv = (float)(cfg.bv - 1 - dv0) - eps;
+                const float na = fmaf(V.Qa[0], dx, fmaf(V.Qa[1], dy, V.Qa[2] * dz0));
+                const float nb = fmaf(V.Qb[0], dx, fmaf(V.Qb[1], dy, V.Qb[2] * dz0));
+                const float w = fmaf(V.Pw[0], dx, fmaf(V.Pw[1], dy, fmaf(V.Pw[2], dz0, V.w0)));
+                const float zl = (float)(BZ - 1);
+                const float w1 = fmaf(zl, V.Pw[2], w);
+                const bool wpos = w > 0.0f && w1 > 0.0f;
+                const float iw0 = wpos ? __frcp_rn(w) : 0.0f, iw1 = wpos ? __frcp_rn(w1) : 0.0f;
+                const float qu0 = fmaf(na, iw0, V.fu), qu1 = fmaf(fmaf(zl, V.Qa[2], na), iw1, V.fu);
+                const float qv0 = fmaf(nb, iw0, V.fv), qv1 = fmaf(fmaf(zl, V.Qb[2], nb), iw1, V.fv);
+                const bool in = wpos && qu0 >= lu && qu0 < hu && qu1 >= lu && qu1 < hu && qv0 >= lvv && qv0 < hvv &&
+                                qv1 >= lvv && qv1 < hvv;
+                if (__all_sync(0xffffffffu, in)) {
+                    const int bu = cfg.bu;
+                    if (V.flat) {
+                        // u and w constant along the column
+                        const float tu = __fadd_rd(qu0, 12582912.0f);
+                        const float au = qu0 - (tu - 12582912.0f);
+                        const T *bc = box + (__float_as_int(tu) - 0x4B400000 + du0);
+                        const float om = W2 ? iw0 * iw0 : 1.0f;
+#pragma unroll
+                        for (int z = 0; z < BZ; ++z) {
+                            const float qv = fmaf(fmaf((float)z, V.Qb[2], nb), iw0, V.fv);
+                            const float t = __fadd_rd(qv, 12582912.0f);
+                            const float av = qv - (t - 12582912.0f);
+                            const T *r = bc + (__float_as_int(t) - 0x4B400000 + dv0) * bu;
+                            const float q00 = to_f32(r[0]), q01 = to_f32(r[1]);
+                            const float q10 = to_f32(r[bu]), q11 = to_f32(r[bu + 1]);
+                            const float r0 = fmaf(au, q01 - q00, q00);
+                            const float r1 = fmaf(au, q11 - q10, q10);
+                            acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int z = 0; z < BZ; ++z) {
+                            const float fz = (float)z;
+                            const float iw = __frcp_rn(fmaf(fz, V.Pw[2], w));
+                            const float qu = fmaf(fmaf(fz, V.Qa[2], na), iw, V.fu);
+                            const float qv = fmaf(fmaf(fz, V.Qb[2], nb), iw, V.fv);
+                            const float tu = __fadd_rd(qu, 12582912.0f), tv = __fadd_rd(qv, 12582912.0f);
+                            const float au = qu - (tu - 12582912.0f), av = qv - (tv - 12582912.0f);
+                            const T *r = box + ((__float_as_int(tv) - 0x4B400000 + dv0) * bu +
+                                                (__float_as_int(tu) - 0x4B400000 + du0));
+                            const float q00 = to_f32(r[0]), q01 = to_f32(r[1]);
+                            const float q10 = to_f32(r[bu]), q11 = to_f32(r[bu + 1]);
+                            const float r0 = fmaf(au, q01 - q00, q00);
+                            const float r1 = fmaf(au, q11 - q10, q10);
+                            const float om = W2 ? iw * iw : 1.0f;
+                            acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
+                        }
+                    }
+                    continue;
+                }
+            }
+            bp_view_global<T, BZ, W2>(V, sb + (long long)n * nv * nu, nu, nv, dx, dy, dz0, acc);
+        }
+        __syncthreads();   // stage s is consumed before it is refilled (two chunks later)
+    }
+    if (lost >= 0) {
+        if (tid == 0) atomicAdd(p.flags + FLAG_TMA_TIMEOUT, 1);
+        // wait (bounded) for the copies still in flight (this chunk's and the next one's) before the
+        // shared memory goes away
+        mbar_wait_bounded(bars[lost & 1], (unsigned)(lost >> 1) & 1u);
+        if (lost + 1 < nchunks) mbar_wait_bounded(bars[(lost + 1) & 1], (unsigned)((lost + 1) >> 1) & 1u);
+        return;
+    }
+    if (i < p.vol.nx && j < p.vol.ny) {
+        T *vb = vol + (long long)b * p.vol_elems;
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) {
+            const int k = bz0 + z;
+            if (k < p.vol.nz) vb[((long long)k * p.vol.ny + j) * p.vol.nx + i] = from_f32<T>(acc[z]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------------------------
+
+namespace {
+
+// Shadow half-extents (pixels) of a 16 x 16 x BZ brick centred at Xb (world mm relative to the volume
+// centre) in view record x, as the device set-up computes them; false where unbounded.
+bool host_shadow(const pyronn_geom *g, const double *x, const double Xb[3], double hz, int &eu, int &ev) {
+    const double s[3] = {g->sx, g->sy, g->sz};
+    double Pa[3], Pb[3], Pw[3], a0, b0, w0;
+    if (g->kind == 1) {
+        for (int i = 0; i < 3; ++i) {
+            Pa[i] = x[i];
+            Pb[i] = x[4 + i];
+            Pw[i] = x[8 + i];
+        }
+        a0 = Pa[0] * Xb[0] + Pa[1] * Xb[1] + Pa[2] * Xb[2] + x[3];
+        b0 = Pb[0] * Xb[0] + Pb[1] * Xb[1] + Pb[2] * Xb[2] + x[7];
+        w0 = Pw[0] * Xb[0] + Pw[1] * Xb[1] + Pw[2] * Xb[2] + x[11];
+    } else {
+        for (int i = 0; i < 3; ++i) {
+            Pa[i] = x[3 + i] / g->du;
+            Pb[i] = x[6 + i] / g->dv;
+            Pw[i] = 0.0;
+        }
+        a0 = b0 = 0.0;
+        w0 = 1.0;
+    }
+    if (!(w0 > 0.0)) return false;
+    const double u0 = a0 / w0, v0 = b0 / w0;
+    const double h[3] = {0.5 * (BPB_X - 1) + 1.0, 0.5 * (BPB_Y - 1) + 1.0, hz + 1.0};
+    double sa = 0.0, sbb = 0.0, sw = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        sa += std::fabs((Pa[i] - u0 * Pw[i]) * s[i]) * h[i];
+        sbb += std::fabs((Pb[i] - v0 * Pw[i]) * s[i]) * h[i];
+        sw += std::fabs(Pw[i] * s[i]) * h[i];
+    }
+    const double wmin = w0 - sw;
+    if (!(wmin > 0.0) || !(sa / wmin < 4096.0) || !(sbb / wmin < 4096.0)) return false;
+    eu = (int)std::ceil(sa / wmin) + 2;
+    ev = (int)std::ceil(sbb / wmin) + 2;
+    return true;
+}
+
+}  // namespace
+
+// Box size for the staged back-projector: the largest shadow over a sample of bricks (every fourth
+// brick along each axis, and the bricks at the volume's corners) and every view, plus the alignment of
+// the box origin. Bricks whose shadow exceeds it take the L1 path. valid = 0 where the sinogram rows are
+// not a multiple of 16 bytes, the volume is 2D, or the box would exceed 40 KB per stage.
+static BpTmaCfg choose_bp_tma_cfg(const pyronn_geom *g, size_t elem, int bz) {
+    BpTmaCfg c{};
+    if (g->ndim != 3 || (g->nu * elem) % 16 != 0 || g->views_ext.empty()) return c;
+    const int nbx = (g->nx + BPB_X - 1) / BPB_X, nby = (g->ny + BPB_Y - 1) / BPB_Y, nbz = (g->nz + bz - 1) / bz;
+    std::vector<int> bxs, bys, bzs;
+    for (int v = 0; v < nbx; v += 4) bxs.push_back(v);
+    for (int v = 0; v < nby; v += 4) bys.push_back(v);
+    for (int v = 0; v < nbz; v += 4) bzs.push_back(v);
+    bxs.push_back(nbx - 1);
+    bys.push_back(nby - 1);
+    bzs.push_back(nbz - 1);
+    const double hz = 0.5 * (bz - 1);
+    std::vector<int> mu(g->n_views, 0), mv(g->n_views, 0);
+    auto work = [&](int v0, int v1) {
+        for (int n = v0; n < v1; ++n) {
+            const double *x = g->views_ext.data() + (size_t)n * VIEW64_STRIDE;
+            for (int a : bxs)
+                for (int bb : bys)
+                    for (int cc : bzs) {
+                        const double Xb[3] = {(a * BPB_X + 0.5 * (BPB_X - 1) - 0.5 * (g->nx - 1)) * g->sx,
+                                              (bb * BPB_Y + 0.5 * (BPB_Y - 1) - 0.5 * (g->ny - 1)) * g->sy,
+                                              (cc * bz + 0.5 * (bz - 1) - 0.5 * (g->nz - 1)) * g->sz};
+                        int eu = 0, ev = 0;
+                        if (host_shadow(g, x, Xb, hz, eu, ev)) {
+                            mu[n] = std::max(mu[n], eu);
+                            mv[n] = std::max(mv[n], ev);
+                        }
+                    }
+        }
+    };
+    const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work, (int)((long long)g->n_views * t / nt),
+                                                  (int)((long long)g->n_views * (t + 1) / nt));
+    work(0, (int)((long long)g->n_views / nt));
+    for (auto &t : th) t.join();
+    int eu = 0, ev = 0;
+    for (int n = 0; n < g->n_views; ++n) {
+        eu = std::max(eu, mu[n]);
+        ev = std::max(ev, mv[n]);
+    }
+    const int align = 16 / (int)elem;
+    int bu = 2 * eu + 1 + (align - 1);
+    bu = (bu + align - 1) / align * align;
+    const int bv = 2 * ev + 1;
+    if (eu <= 0 || bu > 256 || bv > 256) return c;
+    // views per stage: as many (up to BT_CHUNK) as let four CTAs share an SM (228 KB, 1 KB reserved and
+    // the static stage records per CTA)
+    const int stride = (int)((((size_t)bu * bv * elem + 127) / 128) * 128 / elem);
+    const size_t view_bytes = (size_t)stride * elem;
+    const size_t per_cta_fixed = 1024 + sizeof(BtStage) * 2 + 16 + 128;
+    int chunk = BT_CHUNK;
+    while (chunk > 1 && 4 * (per_cta_fixed + 2 * chunk * view_bytes) > 228 * 1024) --chunk;
+    if (2 * chunk * view_bytes > 100 * 1024) return c;
+    c.bu = bu;
+    c.bv = bv;
+    c.stride = stride;
+    c.chunk = chunk;
+    c.valid = 1;
+    return c;
+}
+
+template <typename T, int BZ, bool W2>
+static int launch_bt(const OpParams &p, const BpTmaCfg &cfg, const void *sino, void *vol, cudaStream_t st) {
+    auto enc = tma_encode_fn();
+    if (!enc) return (int)cudaErrorNotSupported;
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    const size_t smem = (size_t)2 * cfg.chunk * cfg.stride * sizeof(T) + 128;
+    auto kern = bp_tma_kernel<T, BZ, W2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    const int nbx = ceil_div(p.vol.nx, BPB_X), nby = ceil_div(p.vol.ny, BPB_Y), nbz = ceil_div(p.vol.nz, BZ);
+    const int per_launch = 65535 / nbz > 0 ? 65535 / nbz : 1;
+    for (int b0 = 0; b0 < p.batch; b0 += per_launch) {
+        const int nb = std::min(p.batch - b0, per_launch);
+        const T *s0 = (const T *)sino + (size_t)b0 * p.sino_elems;
+        // the sinograms of this launch as one 3D array: u, v, view (views of the batch items in order)
+        cuuint64_t gdim[3] = {(cuuint64_t)p.det.nu, (cuuint64_t)p.det.nv, (cuuint64_t)p.n_views * nb};
+        cuuint64_t gstride[2] = {(cuuint64_t)p.det.nu * sizeof(T), (cuuint64_t)p.det.nu * p.det.nv * sizeof(T)};
+        cuuint32_t box[3] = {(cuuint32_t)cfg.bu, (cuuint32_t)cfg.bv, 1};
+        cuuint32_t estride[3] = {1, 1, 1};
+        CUtensorMap map;
+        std::memset(&map, 0, sizeof(map));
+        CUresult r = enc(&map, dt, 3, const_cast<T *>(s0), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return (int)cudaErrorInvalidValue;
+        OpParams q = p;
+        q.batch = nb;
+        dim3 grid(nbx, nby, nbz * nb);
+        kern<<<grid, BPB_NT, smem, st>>>(q, cfg, map, s0, (T *)vol + (size_t)b0 * p.vol_elems);
+    }
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+static int launch_bt_t(const OpParams &p, const BpTmaCfg &cfg, const void *sino, void *vol, cudaStream_t st) {
+    const bool w2 = p.perspective && p.weight == PYRONN_BP_INV_W2;
+    return w2 ? launch_bt<T, 8, true>(p, cfg, sino, vol, st) : launch_bt<T, 8, false>(p, cfg, sino, vol, st);
+}
+
+// The staged back-projector applies (3D, rows of 16-byte multiples, a box of bounded size)?
+bool bp_tma_usable(pyronn_geom *g, int dtype) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    const int k = dtype;
+    if (!g->bpt_ready[k]) {
+        const BpTmaCfg c = choose_bp_tma_cfg(g, dtype_size(dtype), 8);
+        g->bpt_cfg[k][0] = c.bu;
+        g->bpt_cfg[k][1] = c.bv;
+        g->bpt_cfg[k][2] = c.valid;
+        g->bpt_cfg[k][3] = c.chunk;
+        g->bpt_cfg[k][4] = c.stride;
+        g->bpt_ready[k] = 1;
+    }
+    return g->bpt_cfg[k][2] != 0;
+}
+
+int launch_bp_tma(pyronn_geom *g, const OpParams &p, const void *sino, void *vol, int dtype, void *stream) {
+    if (!bp_tma_usable(g, dtype)) return (int)cudaErrorInvalidValue;
+    BpTmaCfg c{};
+    c.bu = g->bpt_cfg[dtype][0];
+    c.bv = g->bpt_cfg[dtype][1];
+    c.chunk = g->bpt_cfg[dtype][3];
+    c.stride = g->bpt_cfg[dtype][4];
+    c.valid = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+        case PYRONN_F32: return launch_bt_t<float>(p, c, sino, vol, st);
+        case PYRONN_BF16: return launch_bt_t<__nv_bfloat16>(p, c, sino, vol, st);
+        case PYRONN_F16: return launch_bt_t<__half>(p, c, sino, vol, st);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pyronn

@@ -36,49 +36,11 @@
 
 #include "device_common.cuh"
 #include "host_rays.h"
+#include "tma_common.cuh"
 
 namespace pyronn {
 
 constexpr int TMA_TU = 16, TMA_TV = 16, TMA_NT = TMA_TU * TMA_TV;
-constexpr unsigned TMA_WAIT_LIMIT = 1u << 20;   // try_wait polls before a copy counts as lost
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-    for (unsigned i = 0; i < TMA_WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *map, unsigned bar, int x, int y, int z,
-                                            int b) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(dst),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(b), "r"(bar)
-        : "memory");
-}
-
 struct TmaMaps {
     CUtensorMap map[3];   // one box shape per march axis
 };
@@ -545,22 +507,22 @@ void tile_extents(const pyronn_geom *g, const FpRec &rec, int tu0, int tv0, int 
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
 
 }  // namespace
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
 
 // Box dimensions for the TMA kernel, or depth = 0 if it cannot be used (shared memory too small or
 // the row pitch is not a multiple of 16 bytes). xt: x-march boxes may come from a y-fastest copy of
@@ -630,7 +592,7 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
     // static shared memory and the per-CTA reservation fit in the SM's 228 KB; else two
     const size_t per_cta = (size_t)c.nbuf * c.buf_elems * elem + 128 + 512 + 1024;
     const int auto_minb = 4 * per_cta <= 228 * 1024 ? 4 : 2;
-    c.minb = minb == 2 || minb == 4 ? minb : auto_minb;
+    c.minb = (minb == 2 || minb == 4 || (minb == 3 && 3 * per_cta <= 228 * 1024)) ? minb : auto_minb;
     return c;
 }
 
@@ -640,7 +602,7 @@ template <typename T>
 static int encode_maps(const OpParams &p, const FpTmaBox &cfg, const void *vol, const void *vt, int nb,
                        CUtensorMap maps[3]) {
     if (cfg.xt && !vt) return (int)cudaErrorInvalidValue;
-    auto enc = encode_fn();
+    auto enc = tma_encode_fn();
     if (!enc) return (int)cudaErrorNotSupported;
     const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -670,7 +632,7 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
                         cudaStream_t st, int make_copy) {
     if (cfg.xt && !vol_t) return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)cfg.nbuf * sizeof(T) * (size_t)cfg.buf_elems + 128;
-    auto kern = cfg.minb == 4 ? fp_tma_kernel<T, 4> : fp_tma_kernel<T, 2>;
+    auto kern = cfg.minb == 4 ? fp_tma_kernel<T, 4> : (cfg.minb == 3 ? fp_tma_kernel<T, 3> : fp_tma_kernel<T, 2>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);

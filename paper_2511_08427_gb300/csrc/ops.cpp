@@ -197,6 +197,22 @@ int pyronn_geom_adjoint_config(pyronn_geom_t g, int *out) {
     return PYRONN_OK;
 }
 
+int pyronn_geom_bp_config(pyronn_geom_t g, int dtype, int *out) {
+    clear_error();
+    if (!g || !out) return set_error(PYRONN_INVALID_ARG, "null argument");
+    if (dtype_size(dtype) == 0) return set_error(PYRONN_UNSUPPORTED_DTYPE, "unsupported dtype %d", dtype);
+    for (int i = 0; i < 8; ++i) out[i] = 0;
+    int kernel = g->bp_variant == 1 ? 1 : 2;
+    if (g->bp_variant == 3 && bp_tma_usable(g, dtype)) kernel = 3;
+    out[0] = kernel;
+    out[1] = kernel == 3 ? g->bpt_cfg[dtype][0] : 0;
+    out[2] = kernel == 3 ? g->bpt_cfg[dtype][1] : 0;
+    out[3] = g->ndim == 2 ? 1 : (kernel == 3 ? 8 : (g->tuning.bp_brick_z ? g->tuning.bp_brick_z : 8));
+    out[4] = kernel == 3 ? g->bpt_cfg[dtype][3] : 0;
+    out[5] = kernel == 3 ? g->bpt_cfg[dtype][4] : 0;
+    return PYRONN_OK;
+}
+
 int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
@@ -211,8 +227,8 @@ int pyronn_geom_set_tuning(pyronn_geom_t g, int param, int value) {
             g->tuning.fp_nbuf = value;
             break;
         case PYRONN_TUNE_FP_CTAS_PER_SM:
-            if (value != 0 && value != 2 && value != 4)
-                return set_error(PYRONN_INVALID_ARG, "CTAs per SM must be 0 (automatic), 2 or 4 (got %d)", value);
+            if (value != 0 && value != 2 && value != 3 && value != 4)
+                return set_error(PYRONN_INVALID_ARG, "CTAs per SM must be 0 (automatic), 2, 3 or 4 (got %d)", value);
             g->tuning.fp_minb = value;
             break;
         case PYRONN_TUNE_ADJ_PITCH:
@@ -260,7 +276,7 @@ int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant) {
     clear_error();
     if (!g) return set_error(PYRONN_INVALID_ARG, "null geometry");
     if (op < 0 || op > 2) return set_error(PYRONN_INVALID_ARG, "unknown operator %d", op);
-    const int vmax = op == 0 ? 5 : (op == 1 ? 3 : 2);
+    const int vmax = op == 0 ? 5 : 3;
     if (variant < 0 || variant > vmax) return set_error(PYRONN_INVALID_ARG, "unknown variant %d", variant);
     if (op == 0) g->fp_variant = variant;
     else if (op == 1) g->adj_variant = variant;
@@ -423,6 +439,8 @@ int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch
     OpParams p = make_params(g, batch);
     p.weight = weight;
     if (g->bp_variant == 1) return cuda_rc(launch_bp(p, sino, vol, dtype, stream), "back-projection launch");
+    if (g->bp_variant == 3 && bp_tma_usable(g, dtype))
+        return cuda_rc(launch_bp_tma(g, p, sino, vol, dtype, stream), "back-projection launch");
     return cuda_rc(launch_bp_brick(p, g->tuning.bp_brick_z, sino, vol, dtype, stream), "back-projection launch");
 }
 

@@ -193,6 +193,8 @@ struct pyronn_geom {
     void *texf_arr = nullptr;      // 3D array of the hardware-filtered texture projector (cudaArray_t)
     unsigned long long texf_obj = 0;   // its texture object (linear filtering, border addressing)
     int texf_dtype = -1;           // element type the array holds
+    int bpt_ready[3] = {0, 0, 0};  // staged back-projector: box chosen (per element type)
+    int bpt_cfg[3][5] = {};        // its box (bu, bv), whether it applies, views per stage, slot stride
     void *d_upd_sino = nullptr;    // work buffers of pyronn_adjoint_update on the unfused kernels
     void *d_upd_vol = nullptr;
     void *d_vol_t = nullptr;           // y-fastest copy of the volume for the TMA forward projector
@@ -215,7 +217,8 @@ struct pyronn_geom {
     int adj_variant = 0;           // 0 auto, 1 atomic scatter, 2 output-stationary bricks, 3 slab-ordered
     pyronn::AdjSlabCfg adj_cfg{};
     int adj_cfg_ready = 0;
-    int bp_variant = 0;            // 0 auto, 1 one thread per voxel (absolute coordinates), 2 bricks
+    int bp_variant = 0;            // 0 auto, 1 one thread per voxel (absolute coordinates), 2 bricks (L1 path),
+                                   // 3 bricks with TMA-staged detector shadows
 };
 
 namespace pyronn {
@@ -251,6 +254,8 @@ int launch_sim_blur(const void *in, void *out, const float *angles, int length, 
                     int dtype, void *stream);
 int launch_fp_tex(pyronn_geom *g, const OpParams &p, const void *vol, void *sino, void *stream);
 bool fp_texf_usable(const pyronn_geom *g, int dtype);
+bool bp_tma_usable(pyronn_geom *g, int dtype);
+int launch_bp_tma(pyronn_geom *g, const OpParams &p, const void *sino, void *vol, int dtype, void *stream);
 int launch_fp_texf(pyronn_geom *g, const OpParams &p, const void *vol, void *sino, int dtype, void *stream);
 int launch_axpy(void *vol, const void *w, float alpha, long long n, int dtype, void *stream);
 int launch_adjoint_slab_batched(const PlanLaunch &L, int dtype, int grid, size_t smem, void *stream);

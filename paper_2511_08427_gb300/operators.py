@@ -175,6 +175,12 @@ class Geometry:
                 "box": [o[4:7], o[7:10], o[10:13]], "buf_elems": o[13], "smem_bytes": o[14],
                 "thread_box_capacity": o[15], "y_fastest_x_march": bool(o[16])}
 
+    def bp_config(self, dtype=torch.float32) -> dict:
+        out = (ctypes.c_int * 8)()
+        check(lib().pyronn_geom_bp_config(self._h, _DTYPES[dtype], out))
+        return {"kernel": out[0], "box": [out[1], out[2]], "brick_z": out[3], "views_per_stage": out[4],
+                "slot_elems": out[5]}
+
     def adjoint_config(self) -> dict:
         out = (ctypes.c_int * 8)()
         check(lib().pyronn_geom_adjoint_config(self._h, out))

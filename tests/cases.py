@@ -99,6 +99,18 @@ SMALL = [
                                     sid=75.0, sdd=120.0, sigma_mm=0.5, sigma_deg=0.2, seed=5), 3),
 ]
 
+def _aligned(case: Case) -> Case:
+    """The same 3D geometry with the detector widened to a multiple of 8 pixels (rows of whole 16-byte
+    groups in every storage type), so that the kernels that copy detector boxes with tensor copies apply."""
+    p = dict(case.params)
+    nv, nu = p["det_shape"]
+    p["det_shape"] = (nv, (nu + 7) // 8 * 8)
+    return Case(case.name + "_det8", p, case.ndim)
+
+
+# Small 3D cases whose detector rows are whole 16-byte groups.
+SMALL_DET8 = [_aligned(c) for c in SMALL if c.ndim == 3]
+
 # The workloads of the benchmark configurations (full sizes).
 CFG1 = Case("cfg1_parallel2d", dict(kind="parallel2d", vol_shape=(128, 128), vol_spacing=(1.0, 1.0), nu=183, du=1.0,
                                     views=180, range=math.pi), 2)

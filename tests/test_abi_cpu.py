@@ -199,12 +199,13 @@ def test_config_invariants_over_random_geometries(L):
     ones: 120 seeded random cone geometries (sizes, anisotropic spacings, offsets, helices, detector
     sizes, steps), each storage type and both x-march staging choices. Wherever the TMA projector is
     chosen, x-march boxes start and stay 16-byte aligned along their innermost axis and fit 200 KB;
-    wherever the slab adjoint is chosen, its box (at most 160 KB) and slab table fit 200 KB."""
+    wherever the slab adjoint is chosen, its box (at most 160 KB) and slab table fit 200 KB; wherever the
+    staged back-projector is chosen, its detector boxes follow the tensor-copy rules."""
     import random
     import torch
     from paper_2511_08427_gb300.operators import TUNE_FP_TRANSPOSE, Geometry
     rnd = random.Random(2024)
-    seen_tma = seen_adj = 0
+    seen_tma = seen_adj = seen_bp = 0
     for _ in range(120):
         shape = tuple(rnd.choice([8, 12, 16, 24, 32, 40, 48, 64, 96]) for _ in range(3))
         sp = tuple(rnd.choice([0.25, 0.4, 0.5, 0.8, 1.0, 2.0]) for _ in range(3))
@@ -234,6 +235,22 @@ def test_config_invariants_over_random_geometries(L):
                     inner = 1 if (m == 0 and c["y_fastest_x_march"]) else 0
                     assert (box[inner] * size) % 16 == 0, (m, box)
                 assert c["smem_bytes"] <= 200 * 1024 + 128
+            g.set_variant(2, 3)
+            b = g.bp_config(td)
+            g.set_variant(2, 0)
+            if b["kernel"] == 3:
+                seen_bp += 1
+                bu, bv = b["box"]
+                # tensor-copy rules: the box's inner extent a multiple of 16 bytes, every extent at most
+                # 256, each view's slot in shared memory a multiple of 128 bytes (its destination must be
+                # 128-byte aligned), two stages within the kernel's shared memory
+                assert (det[1] * size) % 16 == 0
+                assert (bu * size) % 16 == 0 and 1 <= bu <= 256 and 3 <= bv <= 256
+                assert b["slot_elems"] >= bu * bv and (b["slot_elems"] * size) % 128 == 0
+                assert 1 <= b["views_per_stage"] <= 4
+                assert 2 * b["views_per_stage"] * b["slot_elems"] * size <= 100 * 1024
+            else:
+                assert (det[1] * size) % 16 != 0 or b["kernel"] == 2
         a = g.adjoint_config()
         if a["kernel"] == 3:
             seen_adj += 1
@@ -242,7 +259,7 @@ def test_config_invariants_over_random_geometries(L):
             # the box itself at most 160 KB; box and slab table within the 200 KB the kernel is given
             assert a["box_floats"] <= 40 * 1024
             assert 4 * ((a["box_floats"] + 3) // 4 * 4) + 104 * a["max_slabs"] <= 200 * 1024
-    assert seen_tma > 100 and seen_adj > 60
+    assert seen_tma > 100 and seen_adj > 60 and seen_bp > 60
 
 
 def test_adjoint_config_invariants(L):
