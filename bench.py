@@ -390,12 +390,14 @@ def kernel_traffic(kernel: str, workload: str, source: str):
 
 SOURCES = {"fp_tma_kernel": "paper_2511_08427_gb300/csrc/k_fp_tma.cu",
            "adjoint_slab_kernel": "paper_2511_08427_gb300/csrc/k_adjoint_slab.cu",
-           "bp_brick_kernel": "paper_2511_08427_gb300/csrc/k_bp_brick.cu"}
+           "bp_brick_kernel": "paper_2511_08427_gb300/csrc/k_bp_brick.cu",
+           "bp_tma_kernel": "paper_2511_08427_gb300/csrc/k_bp_tma.cu"}
 
 
-def rooflines(rates, mhz, workload, n_samples, n_updates, fp_s, adj_s, bp_s):
+def rooflines(rates, mhz, workload, n_samples, n_updates, fp_s, adj_s, bp_s, bp_kernel=2):
     """Per kernel: the unit that binds it, its algorithmic rate and the measured peak of that unit at the
-    SM clock seen during the timed region; the FP32 (ALU) fraction beside it."""
+    SM clock seen during the timed region; the FP32 (ALU) fraction beside it. bp_kernel: the
+    back-projector that ran (2 brick kernel, L1 taps; 3 staged kernel, shared-memory taps)."""
     from paper_2511_08427_gb300 import roofline as R
     src = (f"roofline_peaks.cu probes: {rates['sms']} SMs x measured rate per SM clock x {mhz:.0f} MHz "
            f"(median SM clock sampled during the timed region)")
@@ -417,9 +419,16 @@ def rooflines(rates, mhz, workload, n_samples, n_updates, fp_s, adj_s, bp_s):
     rl_adj = entry("adjoint_slab_kernel", "smem_atomics", adj_ach, adj_pk, "Gop/s", n_samples * ADJ_FLOP_PER_SAMPLE,
                    adj_s, f"{ADJ_RED_PER_SAMPLE} shared-memory int32 reductions and {ADJ_FLOP_PER_SAMPLE} FLOP per sample")
     bp_ach = n_updates * BP_LOADS_PER_UPDATE / bp_s / 1e9
-    bp_pk = R.peak(rates, "ld_global_l1_b32", mhz) / 1e9
-    rl_bp = entry("bp_brick_kernel", "l1", bp_ach, bp_pk, "Gop/s", n_updates * BP_FLOP_PER_UPDATE, bp_s,
-                  f"{BP_LOADS_PER_UPDATE} L1-hit detector loads and {BP_FLOP_PER_UPDATE} FLOP per voxel-view update")
+    if bp_kernel == 3:
+        bp_pk = R.peak(rates, "ld_shared_b32", mhz) / 1e9
+        rl_bp = entry("bp_tma_kernel", "smem", bp_ach, bp_pk, "Gop/s", n_updates * BP_FLOP_PER_UPDATE, bp_s,
+                      f"{BP_LOADS_PER_UPDATE} shared-memory detector loads and {BP_FLOP_PER_UPDATE} FLOP per "
+                      f"voxel-view update")
+    else:
+        bp_pk = R.peak(rates, "ld_global_l1_b32", mhz) / 1e9
+        rl_bp = entry("bp_brick_kernel", "l1", bp_ach, bp_pk, "Gop/s", n_updates * BP_FLOP_PER_UPDATE, bp_s,
+                      f"{BP_LOADS_PER_UPDATE} L1-hit detector loads and {BP_FLOP_PER_UPDATE} FLOP per voxel-view "
+                      f"update")
     return {"fp": rl_fp, "adjoint": rl_adj, "bp": rl_bp}
 
 
@@ -510,7 +519,8 @@ def run_cone256(dev, steps, rates, mhz):
            "samples_per_fp": n_samples, "updates_per_bp": n_updates, "gd_iteration_ms": gd_ms,
            "fp_bf16": {"ms": fp_bf16_ms, "gsamples_per_s": n_samples / (fp_bf16_ms * 1e-3) / 1e9},
            "fbp_filter_ms": fbp_ms,
-           "rooflines": rooflines(rates, mhz, "cone256", n_samples, n_updates, fp_s, adj_s, bp_s)}
+           "rooflines": rooflines(rates, mhz, "cone256", n_samples, n_updates, fp_s, adj_s, bp_s,
+                                  g.bp_config()["kernel"])}
     del vol, sino, cot, adj, bpv, flush
     torch.cuda.empty_cache()
     return out
@@ -644,7 +654,7 @@ def run_gpu(args):
     clk = clocks.summary()
     mhz = clk["sm_mhz"] or rates["sm_mhz"]
     fp_s, adj_s, bp_s = fp_sum / K * 1e-3, adj_sum / K * 1e-3, bp_sum / K * 1e-3
-    rl = rooflines(rates, mhz, name, n_samples, n_updates, fp_s, adj_s, bp_s)
+    rl = rooflines(rates, mhz, name, n_samples, n_updates, fp_s, adj_s, bp_s, g.bp_config()["kernel"])
     dominant = max(rl.values(), key=lambda r: r["launch_ms"])
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)

@@ -8,9 +8,10 @@
 // projection of the brick centre, sized on the host for the geometry) into shared memory with one 3D
 // tensor copy, whose zero fill stands for the detector's zero padding. Views go in chunks (up to BT_CHUNK
 // views, as many as let four CTAs share an SM) through two shared-memory stages: while the CTA
-// back-projects one chunk, the next chunk's copies are in
-// flight, so the taps are low-latency shared-memory loads instead of first-touch L1 misses, and need no
-// bounds tests. A warp takes the staged path for a view when every lane's column (whose u and v are
+// back-projects one chunk, the next chunk's copies are in flight, so the taps are low-latency
+// shared-memory loads instead of first-touch L1 misses, and need no bounds tests. One barrier per chunk
+// orders the stages. The per-(brick, view) constants (FP64, a unit of low throughput on this GPU) are
+// formed by a full warp for a group of about 32 views at a time, one lane per view. A warp takes the staged path for a view when every lane's column (whose u and v are
 // monotone along z, so its end voxels bound it) falls inside the box with a margin; other warps, and
 // views whose shadow exceeds the box (the box is sized from a sample of bricks), read through L1 as the
 // brick kernel does. Every copy wait is bounded; a lost copy sets FLAG_TMA_TIMEOUT and the CTA leaves.
@@ -26,7 +27,8 @@
 
 namespace pyronn {
 
-constexpr int BT_CHUNK = 4;   // most views per stage (the configuration may use fewer, see cfg.chunk)
+constexpr int BT_CHUNK = 4;    // most views per stage (the configuration may use fewer, see cfg.chunk)
+constexpr int BT_GROUP = 32;   // most views whose set-up one warp computes at once (one lane per view)
 
 struct BpTmaCfg {
     int bu, bv;    // staged box per view (pixels); bu * element size is a multiple of 16 bytes
@@ -36,26 +38,29 @@ struct BpTmaCfg {
     int valid;     // 0: the kernel does not apply (rows not a multiple of 16 bytes, box too large)
 };
 
-struct BtStage {
-    BpView v[BT_CHUNK];
-    int ub[BT_CHUNK], vb[BT_CHUNK];   // box origin on the detector (ub a multiple of 16 bytes / element)
-    int staged[BT_CHUNK];             // 1: the view's shadow fits the box and was copied
+// Set-up records of a group of consecutive views (chunk * floor(BT_GROUP / chunk) of them).
+struct BtGroup {
+    BpView v[BT_GROUP];
+    int ub[BT_GROUP], vb[BT_GROUP];   // box origin on the detector (ub a multiple of 16 bytes / element)
+    int staged[BT_GROUP];             // 1: the view's shadow fits the box and is copied
 };
 
-// Per-view set-up of a stage for views n0 .. n0 + cfg.chunk - 1 (threads 0 .. cfg.chunk - 1).
+// Set-up of views n0 .. n0 + count - 1 (count <= 32) by the lanes of warp 0, one view per lane: the
+// per-(brick, view) constants are formed in FP64, whose throughput is low, so a full warp forms them
+// for a whole group at once rather than a few lanes per stage.
 template <typename T, int BZ>
-__device__ __forceinline__ void bt_setup(const OpParams &p, const BpTmaCfg &cfg, const double Xb[3], int n0,
-                                         BtStage &S) {
+__device__ __forceinline__ void bt_group_setup(const OpParams &p, const BpTmaCfg &cfg, const double Xb[3], int n0,
+                                               int count, BtGroup &G) {
     const int t = threadIdx.x;
-    if (t >= cfg.chunk) return;
+    if (t >= count) return;
     const int n = n0 + t;
-    S.staged[t] = 0;
-    S.ub[t] = S.vb[t] = 0;
+    G.staged[t] = 0;
+    G.ub[t] = G.vb[t] = 0;
+    BpView &V = G.v[t];
     if (n >= p.n_views) {
-        S.v[t].valid = 0;
+        V.valid = 0;
         return;
     }
-    BpView &V = S.v[t];
     bp_view_setup(p, n, Xb, 0.5 * (BZ - 1), V);
     if (!V.valid || V.eu < 0) return;
     constexpr int align = 16 / (int)sizeof(T);
@@ -65,9 +70,9 @@ __device__ __forceinline__ void bt_setup(const OpParams &p, const BpTmaCfg &cfg,
     // the box must hold the taps of every voxel; a box entirely off the detector is all zero and is
     // copied all the same (the copy fills it)
     if (u_hi - ub + 1 <= cfg.bu && 2 * V.ev + 1 <= cfg.bv) {
-        S.ub[t] = ub;
-        S.vb[t] = vb;
-        S.staged[t] = 1;
+        G.ub[t] = ub;
+        G.vb[t] = vb;
+        G.staged[t] = 1;
     }
 }
 
@@ -75,12 +80,14 @@ template <typename T, int BZ, bool W2>
 __global__ void __launch_bounds__(BPB_NT, 4) bp_tma_kernel(OpParams p, BpTmaCfg cfg, const __grid_constant__ CUtensorMap map,
                                                            const T *__restrict__ sino, T *__restrict__ vol) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ BtStage st[2];
+    __shared__ BtGroup grp[2];
     __shared__ unsigned long long bar[2];
     const unsigned raw = smem_u32(smem_raw);
     T *const stage0 = (T *)(smem_raw + (((raw + 127u) & ~127u) - raw));
     const int per_view = cfg.stride;                                  // slot of one view (128-byte multiple)
     const int chunk = cfg.chunk;
+    const int K = BT_GROUP / chunk;                                   // chunks per group (>= 8)
+    const int gsize = K * chunk;                                      // views per group
     const unsigned view_bytes = (unsigned)(sizeof(T) * cfg.bu * cfg.bv);   // bytes one copy delivers
 
     const int nbz = (p.vol.nz + BZ - 1) / BZ;
@@ -108,43 +115,57 @@ __global__ void __launch_bounds__(BPB_NT, 4) bp_tma_kernel(OpParams p, BpTmaCfg 
         mbar_init(bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // thread 0 issues the copies of stage s (its set-up is visible to it after a barrier)
-    auto issue = [&](int n0, int s) {
+    // Chunk ch holds views ch * chunk + c (c < chunk), whose records are entries (ch % K) * chunk + c of
+    // grp[(ch / K) & 1], and goes through stage ch & 1. Thread 0 issues its copies once its group's
+    // set-up is visible (after a barrier) and every thread is done with the chunk that last used the stage.
+    auto issue = [&](int ch) {
+        const BtGroup &G = grp[(ch / K) & 1];
+        const int e0 = (ch % K) * chunk, s = ch & 1;
         unsigned bytes = 0;
-        for (int c = 0; c < chunk; ++c) bytes += st[s].staged[c] ? view_bytes : 0u;
+        for (int c = 0; c < chunk; ++c) bytes += G.staged[e0 + c] ? view_bytes : 0u;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the stage was last read by threads
         mbar_expect_tx(bars[s], bytes);
         for (int c = 0; c < chunk; ++c)
-            if (st[s].staged[c])
-                tma_load_3d(smem_u32(stage0 + (size_t)(s * chunk + c) * per_view), &map, bars[s], st[s].ub[c],
-                            st[s].vb[c], b * p.n_views + n0 + c);
+            if (G.staged[e0 + c])
+                tma_load_3d(smem_u32(stage0 + (size_t)(s * chunk + c) * per_view), &map, bars[s], G.ub[e0 + c],
+                            G.vb[e0 + c], b * p.n_views + ch * chunk + c);
     };
 
     const int nchunks = (p.n_views + chunk - 1) / chunk;
-    bt_setup<T, BZ>(p, cfg, Xb, 0, st[0]);
+    if (tid < 32) bt_group_setup<T, BZ>(p, cfg, Xb, 0, gsize, grp[0]);
     __syncthreads();
-    if (tid == 0) issue(0, 0);
-    int lost = -1;   // the chunk whose copy did not arrive
+    if (tid == 0) issue(0);
+    int lost = -1;        // the first chunk whose copy did not arrive in time (for some thread)
+    int mine_lost = 0;    // this thread's wait ran out
     for (int ch = 0; ch < nchunks; ++ch) {
         const int s = ch & 1;
-        if (ch + 1 < nchunks) bt_setup<T, BZ>(p, cfg, Xb, (ch + 1) * chunk, st[s ^ 1]);
-        __syncthreads();   // stage s ^ 1's set-up is visible; every thread is done with its previous chunk
-        if (tid == 0 && ch + 1 < nchunks) issue((ch + 1) * chunk, s ^ 1);
-        const bool ok = mbar_wait_bounded(bars[s], (unsigned)(ch >> 1) & 1u);
-        if (!__syncthreads_and(ok)) {
-            lost = ch;
+        // records of the next group, before its first chunk's copies are issued: the group they replace
+        // (two back) was finished by every thread at the barrier of an earlier chunk, as K >= 2
+        if (tid < 32 && ch + 1 < nchunks && (ch + 1) % K == 0)
+            bt_group_setup<T, BZ>(p, cfg, Xb, (ch + 1) * chunk, gsize, grp[((ch + 1) / K) & 1]);
+        // the only barrier per chunk: every thread is done with chunk ch - 1 (stage s ^ 1 may be refilled),
+        // the next group's records are visible, and a lost copy seen by any thread ends every thread's loop
+        if (__syncthreads_or(mine_lost)) {
+            lost = ch - 1;
             break;
         }
-        const BtStage &S = st[s];
+        if (tid == 0 && ch + 1 < nchunks) issue(ch + 1);
+        // the lanes of a warp take one decision (the warp votes below need all 32 lanes)
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bars[s], (unsigned)(ch >> 1) & 1u))) {
+            mine_lost = 1;
+            continue;
+        }
+        const BtGroup &G = grp[(ch / K) & 1];
+        const int e0 = (ch % K) * chunk;
         for (int c = 0; c < chunk; ++c) {
             const int n = ch * chunk + c;
             if (n >= p.n_views) break;
-            const BpView &V = S.v[c];
+            const BpView &V = G.v[e0 + c];
             if (!V.valid) continue;
-            if (S.staged[c]) {
+            if (G.staged[e0 + c]) {
                 const T *box = stage0 + (size_t)(s * chunk + c) * per_view;
                 // tap (iu, iv) of the detector is box[(iv - vb) bu + (iu - ub)]; iu = floor(qu) + U0
-                const int du0 = V.U0 - S.ub[c], dv0 = V.V0 - S.vb[c];
+                const int du0 = V.U0 - G.ub[e0 + c], dv0 = V.V0 - G.vb[e0 + c];
                 const float eps = 1e-3f;
                 const float lu = (float)(-du0) + eps, hu = (float)(cfg.bu - 1 - du0) - eps;
                 const float lvv = (float)(-dv0) + eps, hvv = (float)(cfg.bv - 1 - dv0) - eps;
@@ -203,8 +224,9 @@ __global__ void __launch_bounds__(BPB_NT, 4) bp_tma_kernel(OpParams p, BpTmaCfg 
             }
             bp_view_global<T, BZ, W2>(V, sb + (long long)n * nv * nu, nu, nv, dx, dy, dz0, acc);
         }
-        __syncthreads();   // stage s is consumed before it is refilled (two chunks later)
     }
+    // a copy that ran out in the last chunk
+    if (lost < 0 && __syncthreads_or(mine_lost)) lost = nchunks - 1;
     if (lost >= 0) {
         if (tid == 0) atomicAdd(p.flags + FLAG_TMA_TIMEOUT, 1);
         // wait (bounded) for the copies still in flight (this chunk's and the next one's) before the
@@ -324,7 +346,7 @@ static BpTmaCfg choose_bp_tma_cfg(const pyronn_geom *g, size_t elem, int bz) {
     // the static stage records per CTA)
     const int stride = (int)((((size_t)bu * bv * elem + 127) / 128) * 128 / elem);
     const size_t view_bytes = (size_t)stride * elem;
-    const size_t per_cta_fixed = 1024 + sizeof(BtStage) * 2 + 16 + 128;
+    const size_t per_cta_fixed = 1024 + sizeof(BtGroup) * 2 + 16 + 128;
     int chunk = BT_CHUNK;
     while (chunk > 1 && 4 * (per_cta_fixed + 2 * chunk * view_bytes) > 228 * 1024) --chunk;
     if (2 * chunk * view_bytes > 100 * 1024) return c;
