@@ -321,7 +321,7 @@ PYRONN_API int pyronn_adjoint_host(pyronn_geom_t g, const void *sino_host, void 
  * 2 output-stationary bricks accumulated in shared memory, 3 slab-ordered: detector tiles march
  * the volume like the forward projector, scatter into shared-memory slab boxes and add each box to
  * the volume with vector reductions. op 2 = voxel-driven back-projection: variant 0 automatic
- * (= 2; pyronn_autotune picks 3 where it is faster), 1 one thread per voxel in absolute detector
+ * (= 3 where usable, else 2), 1 one thread per voxel in absolute detector
  * coordinates, 2 bricks with
  * detector coordinates relative to the brick centre's projection, taps read through L1, 3 the same
  * bricks with each view's shadow of the brick copied into shared memory by tensor copies, one chunk of
@@ -353,7 +353,9 @@ PYRONN_API int pyronn_geom_set_variant(pyronn_geom_t g, int op, int variant);
  * depth of the slab-ordered adjoint in voxel planes, 2 .. 16 (0 automatic: the deepest of 8, 6, 5, 4 whose
  * box lets two CTAs share an SM; a depth whose box does not fit runs one CTA per SM, or the brick adjoint
  * if the box exceeds 160 KB); PYRONN_TUNE_BP_BRICK_Z: voxels per thread along z of the brick
- * back-projector of 3D volumes, 4, 8 or 16 (0 automatic = 8); PYRONN_TUNE_ADJ_LANES: how the
+ * back-projectors of 3D volumes, 4, 8 or 16 (0 automatic: 16 for volumes of at least 64 planes, else 8;
+ * the staged back-projector, variant 3, takes 16 where the depth is 16 and 8 otherwise);
+ * PYRONN_TUNE_ADJ_LANES: how the
  * slab-ordered adjoint's lanes take the pixels of a tile, 0 automatic (= 1), 1 the 32 lanes of a warp on
  * consecutive pixels of one tile row, 2 in each pass on every other pixel of two rows two pixels apart
  * (rays of adjacent pixels often share a cell, and their reductions then hit the same shared word);

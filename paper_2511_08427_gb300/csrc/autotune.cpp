@@ -17,7 +17,7 @@ struct Candidate {
 
 const Candidate FP_CANDIDATES[] = {{8, 2}, {8, 1}, {4, 2}, {4, 1}, {12, 1}, {16, 1}, {6, 1}};
 const Candidate ADJ_CANDIDATES[] = {{8, 0}, {6, 0}, {5, 0}, {4, 0}, {6, 1}, {4, 1}, {3, 0}};
-const Candidate BP_CANDIDATES[] = {{8, 2}, {4, 2}, {16, 2}, {8, 3}};
+const Candidate BP_CANDIDATES[] = {{8, 2}, {4, 2}, {16, 2}, {8, 3}, {16, 3}};
 
 int apply(pyronn_geom_t g, int op, const Candidate &c) {
     int rc = PYRONN_OK;

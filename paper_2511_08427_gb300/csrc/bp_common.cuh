@@ -181,7 +181,7 @@ __device__ __forceinline__ void bp_view_global(const BpView &V, const T *__restr
             const float zl = (float)(BZ - 1);
             const float w1 = fmaf(zl, V.Pw[2], w);
             const bool wpos = w > 0.0f && w1 > 0.0f;
-            const float iw0 = wpos ? __frcp_rn(w) : 0.0f, iw1 = wpos ? __frcp_rn(w1) : 0.0f;
+            const float iw0 = wpos ? rcp_fast(w) : 0.0f, iw1 = wpos ? rcp_fast(w1) : 0.0f;
             const float qu0 = fmaf(na, iw0, V.fu), qu1 = fmaf(fmaf(zl, V.Qa[2], na), iw1, V.fu);
             const float qv0 = fmaf(nb, iw0, V.fv), qv1 = fmaf(fmaf(zl, V.Qb[2], nb), iw1, V.fv);
             const float eps = 1e-3f;
@@ -193,7 +193,7 @@ __device__ __forceinline__ void bp_view_global(const BpView &V, const T *__restr
 #pragma unroll
                 for (int z = 0; z < BZ; ++z) {
                     const float fz = (float)z;
-                    const float iw = __frcp_rn(fmaf(fz, V.Pw[2], w));
+                    const float iw = rcp_fast(fmaf(fz, V.Pw[2], w));
                     const float qu = fmaf(fmaf(fz, V.Qa[2], na), iw, V.fu);
                     const float qv = fmaf(fmaf(fz, V.Qb[2], nb), iw, V.fv);
                     const float tu = __fadd_rd(qu, 12582912.0f), tv = __fadd_rd(qv, 12582912.0f);
@@ -213,7 +213,7 @@ __device__ __forceinline__ void bp_view_global(const BpView &V, const T *__restr
 #pragma unroll
         for (int z = 0; z < BZ; ++z) {
             if (w > 0.0f) {
-                const float iw = __frcp_rn(w);
+                const float iw = rcp_fast(w);
                 int iu, iv;
                 float au, av;
                 magic_floor(fmaf(na, iw, V.fu), iu, au);

@@ -84,6 +84,15 @@ __device__ __forceinline__ f32x2 lerp2(f32x2 t, f32x2 a, f32x2 b) {
     return r;
 }
 
+// 1 / x by the hardware's approximate reciprocal (one instruction, relative error of the order of
+// 2^-23; subnormal x gives infinity): for voxel-driven depth weights, whose positions on the detector
+// are offsets of at most a few tens of pixels times 1 / w, so the error stays near 1e-5 pixel
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---------------------------------------------------------------------------------------------
 // rays
 // ---------------------------------------------------------------------------------------------

@@ -34,8 +34,10 @@ struct BpTmaCfg {
     int bu, bv;    // staged box per view (pixels); bu * element size is a multiple of 16 bytes
     int stride;    // elements between the views' boxes in shared memory: a tensor copy's destination must
                    // be 128-byte aligned, so bu * bv rounded up to a multiple of 128 bytes
-    int chunk;     // views per stage (1 .. BT_CHUNK): as many as let four CTAs share an SM
+    int chunk;     // views per stage (1 .. BT_CHUNK): as many as let four CTAs (three for 16-voxel
+                   // columns) share an SM
     int valid;     // 0: the kernel does not apply (rows not a multiple of 16 bytes, box too large)
+    int bz;        // voxels per thread along z (8 or 16)
 };
 
 // Set-up records of a group of consecutive views (chunk * floor(BT_GROUP / chunk) of them).
@@ -77,7 +79,7 @@ __device__ __forceinline__ void bt_group_setup(const OpParams &p, const BpTmaCfg
 }
 
 template <typename T, int BZ, bool W2>
-__global__ void __launch_bounds__(BPB_NT, 4) bp_tma_kernel(OpParams p, BpTmaCfg cfg, const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(BPB_NT, BZ > 8 ? 3 : 4) bp_tma_kernel(OpParams p, BpTmaCfg cfg, const __grid_constant__ CUtensorMap map,
                                                            const T *__restrict__ sino, T *__restrict__ vol) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ BtGroup grp[2];
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(BPB_NT, 4) bp_tma_kernel(OpParams p, BpTmaCfg 
                 const float zl = (float)(BZ - 1);
                 const float w1 = fmaf(zl, V.Pw[2], w);
                 const bool wpos = w > 0.0f && w1 > 0.0f;
-                const float iw0 = wpos ? __frcp_rn(w) : 0.0f, iw1 = wpos ? __frcp_rn(w1) : 0.0f;
+                const float iw0 = wpos ? rcp_fast(w) : 0.0f, iw1 = wpos ? rcp_fast(w1) : 0.0f;
                 const float qu0 = fmaf(na, iw0, V.fu), qu1 = fmaf(fmaf(zl, V.Qa[2], na), iw1, V.fu);
                 const float qv0 = fmaf(nb, iw0, V.fv), qv1 = fmaf(fmaf(zl, V.Qb[2], nb), iw1, V.fv);
                 const bool in = wpos && qu0 >= lu && qu0 < hu && qu1 >= lu && qu1 < hu && qv0 >= lvv && qv0 < hvv &&
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(BPB_NT, 4) bp_tma_kernel(OpParams p, BpTmaCfg 
 #pragma unroll
                         for (int z = 0; z < BZ; ++z) {
                             const float fz = (float)z;
-                            const float iw = __frcp_rn(fmaf(fz, V.Pw[2], w));
+                            const float iw = rcp_fast(fmaf(fz, V.Pw[2], w));
                             const float qu = fmaf(fmaf(fz, V.Qa[2], na), iw, V.fu);
                             const float qv = fmaf(fmaf(fz, V.Qb[2], nb), iw, V.fv);
                             const float tu = __fadd_rd(qu, 12582912.0f), tv = __fadd_rd(qv, 12582912.0f);
@@ -338,23 +340,25 @@ static BpTmaCfg choose_bp_tma_cfg(const pyronn_geom *g, size_t elem, int bz) {
         ev = std::max(ev, mv[n]);
     }
     const int align = 16 / (int)elem;
+    const int ctas = bz > 8 ? 3 : 4;   // CTAs per SM the kernel is compiled for
     int bu = 2 * eu + 1 + (align - 1);
     bu = (bu + align - 1) / align * align;
     const int bv = 2 * ev + 1;
     if (eu <= 0 || bu > 256 || bv > 256) return c;
-    // views per stage: as many (up to BT_CHUNK) as let four CTAs share an SM (228 KB, 1 KB reserved and
-    // the static stage records per CTA)
+    // views per stage: as many (up to BT_CHUNK) as let the CTAs share an SM (228 KB, 1 KB reserved and
+    // the static set-up records per CTA)
     const int stride = (int)((((size_t)bu * bv * elem + 127) / 128) * 128 / elem);
     const size_t view_bytes = (size_t)stride * elem;
     const size_t per_cta_fixed = 1024 + sizeof(BtGroup) * 2 + 16 + 128;
     int chunk = BT_CHUNK;
-    while (chunk > 1 && 4 * (per_cta_fixed + 2 * chunk * view_bytes) > 228 * 1024) --chunk;
+    while (chunk > 1 && ctas * (per_cta_fixed + 2 * chunk * view_bytes) > 228 * 1024) --chunk;
     if (2 * chunk * view_bytes > 100 * 1024) return c;
     c.bu = bu;
     c.bv = bv;
     c.stride = stride;
     c.chunk = chunk;
     c.valid = 1;
+    c.bz = bz;
     return c;
 }
 
@@ -396,20 +400,25 @@ static int launch_bt(const OpParams &p, const BpTmaCfg &cfg, const void *sino, v
 template <typename T>
 static int launch_bt_t(const OpParams &p, const BpTmaCfg &cfg, const void *sino, void *vol, cudaStream_t st) {
     const bool w2 = p.perspective && p.weight == PYRONN_BP_INV_W2;
+    if (cfg.bz == 16)
+        return w2 ? launch_bt<T, 16, true>(p, cfg, sino, vol, st) : launch_bt<T, 16, false>(p, cfg, sino, vol, st);
     return w2 ? launch_bt<T, 8, true>(p, cfg, sino, vol, st) : launch_bt<T, 8, false>(p, cfg, sino, vol, st);
 }
 
-// The staged back-projector applies (3D, rows of 16-byte multiples, a box of bounded size)?
+// The staged back-projector applies (3D, rows of 16-byte multiples, a box of bounded size)? Its columns
+// are 16 voxels deep where the brick depth (bp_brick_depth) is 16, else 8.
 bool bp_tma_usable(pyronn_geom *g, int dtype) {
     std::lock_guard<std::mutex> lk(g->mu);
     const int k = dtype;
-    if (!g->bpt_ready[k]) {
-        const BpTmaCfg c = choose_bp_tma_cfg(g, dtype_size(dtype), 8);
+    const int bz = bp_brick_depth(g->tuning.bp_brick_z, g->nz) == 16 ? 16 : 8;
+    if (!g->bpt_ready[k] || g->bpt_cfg[k][5] != bz) {
+        const BpTmaCfg c = choose_bp_tma_cfg(g, dtype_size(dtype), bz);
         g->bpt_cfg[k][0] = c.bu;
         g->bpt_cfg[k][1] = c.bv;
         g->bpt_cfg[k][2] = c.valid;
         g->bpt_cfg[k][3] = c.chunk;
         g->bpt_cfg[k][4] = c.stride;
+        g->bpt_cfg[k][5] = bz;
         g->bpt_ready[k] = 1;
     }
     return g->bpt_cfg[k][2] != 0;
@@ -422,6 +431,7 @@ int launch_bp_tma(pyronn_geom *g, const OpParams &p, const void *sino, void *vol
     c.bv = g->bpt_cfg[dtype][1];
     c.chunk = g->bpt_cfg[dtype][3];
     c.stride = g->bpt_cfg[dtype][4];
+    c.bz = g->bpt_cfg[dtype][5];
     c.valid = 1;
     cudaStream_t st = (cudaStream_t)stream;
     switch (dtype) {

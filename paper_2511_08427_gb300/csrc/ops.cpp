@@ -203,11 +203,11 @@ int pyronn_geom_bp_config(pyronn_geom_t g, int dtype, int *out) {
     if (dtype_size(dtype) == 0) return set_error(PYRONN_UNSUPPORTED_DTYPE, "unsupported dtype %d", dtype);
     for (int i = 0; i < 8; ++i) out[i] = 0;
     int kernel = g->bp_variant == 1 ? 1 : 2;
-    if (g->bp_variant == 3 && bp_tma_usable(g, dtype)) kernel = 3;
+    if ((g->bp_variant == 3 || g->bp_variant == 0) && bp_tma_usable(g, dtype)) kernel = 3;
     out[0] = kernel;
     out[1] = kernel == 3 ? g->bpt_cfg[dtype][0] : 0;
     out[2] = kernel == 3 ? g->bpt_cfg[dtype][1] : 0;
-    out[3] = g->ndim == 2 ? 1 : (kernel == 3 ? 8 : (g->tuning.bp_brick_z ? g->tuning.bp_brick_z : 8));
+    out[3] = g->ndim == 2 ? 1 : (kernel == 3 ? g->bpt_cfg[dtype][5] : bp_brick_depth(g->tuning.bp_brick_z, g->nz));
     out[4] = kernel == 3 ? g->bpt_cfg[dtype][3] : 0;
     out[5] = kernel == 3 ? g->bpt_cfg[dtype][4] : 0;
     return PYRONN_OK;
@@ -439,9 +439,10 @@ int pyronn_bp(pyronn_geom_t g, const void *sino, void *vol, int dtype, int batch
     OpParams p = make_params(g, batch);
     p.weight = weight;
     if (g->bp_variant == 1) return cuda_rc(launch_bp(p, sino, vol, dtype, stream), "back-projection launch");
-    if (g->bp_variant == 3 && bp_tma_usable(g, dtype))
+    if ((g->bp_variant == 3 || g->bp_variant == 0) && bp_tma_usable(g, dtype))
         return cuda_rc(launch_bp_tma(g, p, sino, vol, dtype, stream), "back-projection launch");
-    return cuda_rc(launch_bp_brick(p, g->tuning.bp_brick_z, sino, vol, dtype, stream), "back-projection launch");
+    return cuda_rc(launch_bp_brick(p, bp_brick_depth(g->tuning.bp_brick_z, g->nz), sino, vol, dtype, stream),
+                   "back-projection launch");
 }
 
 int pyronn_bp_transpose(pyronn_geom_t g, const void *vol, void *sino, int dtype, int batch, int weight,

@@ -151,10 +151,16 @@ struct Tuning {
     int fp_transpose = 0;      // TMA forward projector, x-march tiles: 0 y-fastest copy where usable, 1 never
     int adj_pitch = 0;         // slab adjoint, x-march boxes: 0 odd row pitch where it fits, 1 16-byte pitch
     int adj_depth = 0;         // slab adjoint: slab depth (0 automatic: the deepest that fits two CTAs per SM)
-    int bp_brick_z = 0;        // brick back-projector: voxels per thread along z (0 automatic = 8; 4, 8 or 16)
+    int bp_brick_z = 0;        // brick back-projectors: voxels per thread along z (4, 8 or 16; 0 automatic, see
+                               // bp_brick_depth)
     int adj_lanes = 0;         // slab adjoint lane-to-pixel mapping (0 automatic, 1 tile rows, 2 interleaved)
     int fp_packed = 0;         // TMA forward projector: 0 automatic (= 3), 1 scalar, 2 packed lerps, 3 packed lerps and positions
 };
+
+// Voxels per thread along z of the brick back-projectors for a volume of nz planes: the tuning value,
+// or automatically 16 for volumes of at least 64 planes (the per-view set-up of a column is then spread
+// over twice the voxels) and 8 below.
+inline int bp_brick_depth(int tuning, int nz) { return tuning ? tuning : (nz >= 64 ? 16 : 8); }
 
 }  // namespace pyronn
 
@@ -194,7 +200,7 @@ struct pyronn_geom {
     unsigned long long texf_obj = 0;   // its texture object (linear filtering, border addressing)
     int texf_dtype = -1;           // element type the array holds
     int bpt_ready[3] = {0, 0, 0};  // staged back-projector: box chosen (per element type)
-    int bpt_cfg[3][5] = {};        // its box (bu, bv), whether it applies, views per stage, slot stride
+    int bpt_cfg[3][6] = {};        // its box (bu, bv), whether it applies, views per stage, slot stride, brick depth
     void *d_upd_sino = nullptr;    // work buffers of pyronn_adjoint_update on the unfused kernels
     void *d_upd_vol = nullptr;
     void *d_vol_t = nullptr;           // y-fastest copy of the volume for the TMA forward projector

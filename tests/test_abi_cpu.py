@@ -169,7 +169,7 @@ def test_fp_config_invariants(L, dtype_size, dtype):
     x-march boxes staged from the y-fastest copy), first slab plane minus the guard aligned (so
     x-march boxes of the x-fastest volume start aligned), double buffer within 200 KB."""
     import torch
-    from paper_2511_08427_gb300.operators import TUNE_FP_TRANSPOSE, Geometry
+    from paper_2511_08427_gb300.operators import TUNE_BP_BRICK_Z, TUNE_FP_TRANSPOSE, Geometry
     td = getattr(torch, dtype)
     g = Geometry.cone_circular((64, 96, 128), (0.5, 0.5, 0.5), (100, 130), (0.6, 0.6), 40, 2 * math.pi, 750.0, 1200.0)
     for transpose in (0, 1):
@@ -203,7 +203,7 @@ def test_config_invariants_over_random_geometries(L):
     staged back-projector is chosen, its detector boxes follow the tensor-copy rules."""
     import random
     import torch
-    from paper_2511_08427_gb300.operators import TUNE_FP_TRANSPOSE, Geometry
+    from paper_2511_08427_gb300.operators import TUNE_BP_BRICK_Z, TUNE_FP_TRANSPOSE, Geometry
     rnd = random.Random(2024)
     seen_tma = seen_adj = seen_bp = 0
     for _ in range(120):
@@ -236,21 +236,25 @@ def test_config_invariants_over_random_geometries(L):
                     assert (box[inner] * size) % 16 == 0, (m, box)
                 assert c["smem_bytes"] <= 200 * 1024 + 128
             g.set_variant(2, 3)
-            b = g.bp_config(td)
+            for bz in (8, 16):
+                g.set_tuning(TUNE_BP_BRICK_Z, bz)
+                b = g.bp_config(td)
+                if b["kernel"] == 3:
+                    seen_bp += 1
+                    bu, bv = b["box"]
+                    # tensor-copy rules: the box's inner extent a multiple of 16 bytes, every extent at
+                    # most 256, each view's slot in shared memory a multiple of 128 bytes (its destination
+                    # must be 128-byte aligned), two stages within the kernel's shared memory
+                    assert b["brick_z"] == bz
+                    assert (det[1] * size) % 16 == 0
+                    assert (bu * size) % 16 == 0 and 1 <= bu <= 256 and 3 <= bv <= 256
+                    assert b["slot_elems"] >= bu * bv and (b["slot_elems"] * size) % 128 == 0
+                    assert 1 <= b["views_per_stage"] <= 4
+                    assert 2 * b["views_per_stage"] * b["slot_elems"] * size <= 100 * 1024
+                else:
+                    assert (det[1] * size) % 16 != 0 or b["kernel"] == 2
+            g.set_tuning(TUNE_BP_BRICK_Z, 0)
             g.set_variant(2, 0)
-            if b["kernel"] == 3:
-                seen_bp += 1
-                bu, bv = b["box"]
-                # tensor-copy rules: the box's inner extent a multiple of 16 bytes, every extent at most
-                # 256, each view's slot in shared memory a multiple of 128 bytes (its destination must be
-                # 128-byte aligned), two stages within the kernel's shared memory
-                assert (det[1] * size) % 16 == 0
-                assert (bu * size) % 16 == 0 and 1 <= bu <= 256 and 3 <= bv <= 256
-                assert b["slot_elems"] >= bu * bv and (b["slot_elems"] * size) % 128 == 0
-                assert 1 <= b["views_per_stage"] <= 4
-                assert 2 * b["views_per_stage"] * b["slot_elems"] * size <= 100 * 1024
-            else:
-                assert (det[1] * size) % 16 != 0 or b["kernel"] == 2
         a = g.adjoint_config()
         if a["kernel"] == 3:
             seen_adj += 1

@@ -355,19 +355,21 @@ def test_bp_matches_oracle(ops, case, weight, variant):
     assert g.read_flags()[:4] == [0, 0, 0, 0]
 
 
+@pytest.mark.parametrize("bz", [8, 16])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
 @pytest.mark.parametrize("weight", [0, 1])
 @pytest.mark.parametrize("case", SMALL_DET8, ids=lambda c: c.name)
-def test_staged_bp_matches_oracle_and_l1_path(ops, case, weight, dtype):
-    """The back-projector with TMA-staged detector shadows (variant 3) against the oracle (fed the same
-    rounded sinogram) and against the L1-path brick kernel, in every storage type; the staged box is the
-    one the geometry reports."""
+def test_staged_bp_matches_oracle_and_l1_path(ops, case, weight, dtype, bz):
+    """The back-projector with TMA-staged detector shadows (variant 3; columns of 8 or 16 voxels) against
+    the oracle (fed the same rounded sinogram) and against the L1-path brick kernel, in every storage type;
+    the staged box is the one the geometry reports."""
     g = case.library_geometry()
     og = case.oracle_geometry()
     q = to_dev(inputs.uniform(og.sino_shape, seed=11), dtype)
+    g.set_tuning(ops.TUNE_BP_BRICK_Z, bz)
     g.set_variant(2, 3)
     c = g.bp_config(dtype)
-    assert c["kernel"] == 3
+    assert c["kernel"] == 3 and c["brick_z"] == bz
     assert c["box"][0] * q.element_size() % 16 == 0 and c["box"][1] >= 3
     staged = host(ops.back_project(q, g, weight))
     g.set_variant(2, 2)
