@@ -50,11 +50,14 @@ struct SlabBox {
     int fits;       // the tile's footprint in this slab fits the box
 };
 
+constexpr int FP_RING = 16;   // slab boxes computed ahead, one per lane of warp 0
+
 struct FpTmaShared {
     unsigned long long bar[2];
     float corner[5][6];
     int srange[2];
-    SlabBox box[2];   // boxes of the slabs in the two copy slots (written by the issuing thread)
+    SlabBox box[2];         // boxes of the slabs in the two copy slots (written by the issuing thread)
+    SlabBox ring[FP_RING];  // boxes of the next slabs of the tile (warp 0 only)
 };
 
 // One detector tile (tile_x, tile_y) of one view of volume b: returns false if a tensor copy was lost
@@ -182,11 +185,23 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
         return sb;
     };
 
+    // The lanes of warp 0 compute the boxes of FP_RING slabs at a time (slab s_first + i0 + lane) into a
+    // ring that only warp 0 touches; thread 0 reads a slab's box there when it issues the slab's copy, so
+    // the corner-ray arithmetic is off the path between a slab's barrier and its copy. Called by all 32
+    // lanes of warp 0.
+    auto fill_ring = [&](int i0) {
+        const int lane = tid & 31;
+        __syncwarp();   // thread 0 has read the entries this call replaces
+        if (lane < FP_RING && i0 + lane < nsl) sh.ring[lane] = slab_box(s_first + i0 + lane);
+        __syncwarp();
+    };
+
     float acc = 0.0f;
     const float hdt = 0.5f * p.dt;
     if (nsl > 0) {
+        if (tid < 32) fill_ring(0);
         if (tid == 0) {
-            const SlabBox sb0 = slab_box(s_first);
+            const SlabBox sb0 = sh.ring[0];
             sh.box[0] = sb0;
             mbar_expect_tx(bars[0], box_bytes);
             tma_load_4d(smem_u32(buf0), tmap, bars[0], yt ? sb0.lo[1] : sb0.lo[0], yt ? sb0.lo[0] : sb0.lo[1],
@@ -196,13 +211,16 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
             const int s = s_first + i;
             const int bi = dbl ? (i & 1) : 0;
             const unsigned parity = ph[bi] & 1u;
-            if (dbl && tid == 0 && i + 1 < nsl) {
-                const SlabBox sbn = slab_box(s + 1);
-                sh.box[(i + 1) & 1] = sbn;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(bars[bi ^ 1], box_bytes);
-                tma_load_4d(smem_u32(bi ? buf0 : buf1), tmap, bars[bi ^ 1], yt ? sbn.lo[1] : sbn.lo[0],
-                            yt ? sbn.lo[0] : sbn.lo[1], sbn.lo[2], b);
+            if (dbl && tid < 32 && i + 1 < nsl) {
+                if ((i + 1) % FP_RING == 0) fill_ring(i + 1);
+                if (tid == 0) {
+                    const SlabBox sbn = sh.ring[(i + 1) % FP_RING];
+                    sh.box[(i + 1) & 1] = sbn;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(bars[bi ^ 1], box_bytes);
+                    tma_load_4d(smem_u32(bi ? buf0 : buf1), tmap, bars[bi ^ 1], yt ? sbn.lo[1] : sbn.lo[0],
+                                yt ? sbn.lo[0] : sbn.lo[1], sbn.lo[2], b);
+                }
             }
             // a copy lost anywhere aborts every CTA at its next slab, so the launch ends promptly (the
             // flag is read before the wait so that the two latencies overlap)
@@ -350,13 +368,16 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 }
             }
             __syncthreads();   // everyone is done with this buffer before it is refilled
-            if (!dbl && tid == 0 && i + 1 < nsl) {
-                const SlabBox sbn = slab_box(s + 1);
-                sh.box[(i + 1) & 1] = sbn;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(bars[0], box_bytes);
-                tma_load_4d(smem_u32(buf0), tmap, bars[0], yt ? sbn.lo[1] : sbn.lo[0], yt ? sbn.lo[0] : sbn.lo[1],
-                            sbn.lo[2], b);
+            if (!dbl && tid < 32 && i + 1 < nsl) {
+                if ((i + 1) % FP_RING == 0) fill_ring(i + 1);
+                if (tid == 0) {
+                    const SlabBox sbn = sh.ring[(i + 1) % FP_RING];
+                    sh.box[(i + 1) & 1] = sbn;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(bars[0], box_bytes);
+                    tma_load_4d(smem_u32(buf0), tmap, bars[0], yt ? sbn.lo[1] : sbn.lo[0],
+                                yt ? sbn.lo[0] : sbn.lo[1], sbn.lo[2], b);
+                }
             }
         }
     }
