@@ -375,23 +375,33 @@ def cpu_baseline_leg(name, vol_np, g, dev, results):
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 
-def kernel_traffic(kernel: str, workload: str, source: str):
+def source_digest(files) -> str:
+    """SHA-1 of the concatenated bytes of a kernel's source files (its .cu and the headers it includes)."""
+    h = hashlib.sha1()
+    for name in files:
+        with open(os.path.join(ROOT, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(kernel: str, workload: str, sources):
     """DRAM bytes per launch from the committed ncu record, if it was taken on the current source."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        with open(os.path.join(ROOT, source), "rb") as f:
-            digest = hashlib.sha1(f.read()).hexdigest()
+        digest = source_digest(sources)
     except (OSError, ValueError):
         return None
     return rec.get("dram_bytes_per_launch") if rec.get("source_sha1") == digest else None
 
 
-SOURCES = {"fp_tma_kernel": "paper_2511_08427_gb300/csrc/k_fp_tma.cu",
-           "adjoint_slab_kernel": "paper_2511_08427_gb300/csrc/k_adjoint_slab.cu",
-           "bp_brick_kernel": "paper_2511_08427_gb300/csrc/k_bp_brick.cu",
-           "bp_tma_kernel": "paper_2511_08427_gb300/csrc/k_bp_tma.cu"}
+_CSRC = "paper_2511_08427_gb300/csrc/"
+SOURCES = {"fp_tma_kernel": [_CSRC + f for f in ("k_fp_tma.cu", "device_common.cuh", "tma_common.cuh")],
+           "adjoint_slab_kernel": [_CSRC + f for f in ("k_adjoint_slab.cu", "device_common.cuh")],
+           "bp_brick_kernel": [_CSRC + f for f in ("k_bp_brick.cu", "bp_common.cuh", "device_common.cuh")],
+           "bp_tma_kernel": [_CSRC + f for f in ("k_bp_tma.cu", "bp_common.cuh", "device_common.cuh",
+                                                 "tma_common.cuh")]}
 
 
 def rooflines(rates, mhz, workload, n_samples, n_updates, fp_s, adj_s, bp_s, bp_kernel=2):
@@ -760,6 +770,11 @@ def run_profile(args):
     dev = torch.device("cuda", 0)
     dt = getattr(torch, args.dtype)
     g = make_geometry(args.workload, args.views)
+    if args.params:
+        # the autotuner's parameters of the operator (as the bench line's "autotune" record reports them)
+        from paper_2511_08427_gb300 import autotune
+        a, b = (int(x) for x in args.params.split(","))
+        autotune.apply(g, autotune.OPS[{"fp": "fp", "adj": "adjoint", "bp": "bp"}[args.profile]], a, b)
     if args.variant:
         g.set_variant(0 if args.profile == "fp" else (1 if args.profile == "adj" else 2), args.variant)
     vol = torch.from_numpy(build_volume(args.workload)).to(dev).to(dt)
@@ -810,6 +825,8 @@ def main():
     ap.add_argument("--views", type=int, default=None, help="--profile: keep this many of the workload's views")
     ap.add_argument("--repeat", type=int, default=2, help="--profile: launches after the warm-up launch")
     ap.add_argument("--variant", type=int, default=0, help="--profile: kernel variant of the operator (0 automatic)")
+    ap.add_argument("--params", default=None,
+                    help="--profile: autotuner parameters 'a,b' of fp, adj or bp to apply (as in the bench line)")
     ap.add_argument("--dtype", default="float32", choices=["float32", "bfloat16", "float16"])
     ap.add_argument("--time", action="store_true", help="--profile: print the mean time per launch")
     args = ap.parse_args()

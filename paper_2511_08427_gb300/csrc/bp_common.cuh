@@ -121,7 +121,7 @@ __device__ __forceinline__ void bp_view_global(const BpView &V, const T *__restr
         // so the first and last voxel bound it; if all lanes' four taps lie on the detector, the
         // warp reads them without bounds tests
         const bool wpos = w > 0.0f;
-        const float iw = wpos ? __frcp_rn(w) : 0.0f;
+        const float iw = wpos ? rcp_fast(w) : 0.0f;
         const float qu = fmaf(na, iw, V.fu);
         const float qv0 = fmaf(nb, iw, V.fv), qv1 = fmaf(fmaf((float)(BZ - 1), V.Qb[2], nb), iw, V.fv);
         const float lu = -(float)V.U0, hu = (float)(nu - 1 - V.U0);
