@@ -138,10 +138,10 @@ __device__ __forceinline__ void bp_view_global(const BpView &V, const T *__restr
                 const float t = __fadd_rd(qv, 12582912.0f);
                 const float av = qv - (t - 12582912.0f);
                 const T *r = qc + (__float_as_int(t) - 0x4B400000 + V.V0) * nu;
-                const float q00 = ldg_f32(r), q01 = ldg_f32(r + 1);
-                const float q10 = ldg_f32(r + nu), q11 = ldg_f32(r + nu + 1);
-                const float r0 = fmaf(au, q01 - q00, q00);
-                const float r1 = fmaf(au, q11 - q10, q10);
+                // the two lerps along u as one packed FP32x2 pair (each lane rounds as the scalar FMA)
+                const f32x2 rr = lerp2(splat2(au), pack2(ldg_f32(r), ldg_f32(r + nu)),
+                                       pack2(ldg_f32(r + 1), ldg_f32(r + nu + 1)));
+                const float r0 = lo2(rr), r1 = hi2(rr);
                 acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
             }
             return;
@@ -190,22 +190,23 @@ __device__ __forceinline__ void bp_view_global(const BpView &V, const T *__restr
             const bool ok = wpos && qu0 >= lu && qu0 < hu && qu1 >= lu && qu1 < hu && qv0 >= lv && qv0 < hv &&
                             qv1 >= lv && qv1 < hv;
             if (__all_sync(0xffffffffu, ok)) {
+                // (u, v) positions and the two lerps along u as packed FP32x2 pairs (bit-identical lanes)
+                const f32x2 M2 = splat2(12582912.0f);
+                const f32x2 qab2 = pack2(V.Qa[2], V.Qb[2]), nab2 = pack2(na, nb), fuv2 = pack2(V.fu, V.fv);
 #pragma unroll
                 for (int z = 0; z < BZ; ++z) {
                     const float fz = (float)z;
                     const float iw = rcp_fast(fmaf(fz, V.Pw[2], w));
-                    const float qu = fmaf(fmaf(fz, V.Qa[2], na), iw, V.fu);
-                    const float qv = fmaf(fmaf(fz, V.Qb[2], nb), iw, V.fv);
-                    const float tu = __fadd_rd(qu, 12582912.0f), tv = __fadd_rd(qv, 12582912.0f);
-                    const float au = qu - (tu - 12582912.0f), av = qv - (tv - 12582912.0f);
-                    const T *r = q + ((__float_as_int(tv) - 0x4B400000 + V.V0) * nu +
-                                      (__float_as_int(tu) - 0x4B400000 + V.U0));
-                    const float q00 = ldg_f32(r), q01 = ldg_f32(r + 1);
-                    const float q10 = ldg_f32(r + nu), q11 = ldg_f32(r + nu + 1);
-                    const float r0 = fmaf(au, q01 - q00, q00);
-                    const float r1 = fmaf(au, q11 - q10, q10);
+                    const f32x2 qq = fma2(fma2(splat2(fz), qab2, nab2), splat2(iw), fuv2);
+                    const f32x2 t = add2_rd(qq, M2);
+                    const f32x2 a = sub2(qq, sub2(t, M2));
+                    const T *r = q + ((__float_as_int(hi2(t)) - 0x4B400000 + V.V0) * nu +
+                                      (__float_as_int(lo2(t)) - 0x4B400000 + V.U0));
+                    const f32x2 rr = lerp2(splat2(lo2(a)), pack2(ldg_f32(r), ldg_f32(r + nu)),
+                                           pack2(ldg_f32(r + 1), ldg_f32(r + nu + 1)));
+                    const float r0 = lo2(rr), r1 = hi2(rr);
                     const float om = W2 ? iw * iw : 1.0f;
-                    acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
+                    acc[z] = fmaf(om, fmaf(hi2(a), r1 - r0, r0), acc[z]);
                 }
                 return;
             }

@@ -183,42 +183,50 @@ __global__ void __launch_bounds__(BPB_NT, BZ > 8 ? 3 : 4) bp_tma_kernel(OpParams
                 const bool in = wpos && qu0 >= lu && qu0 < hu && qu1 >= lu && qu1 < hu && qv0 >= lvv && qv0 < hvv &&
                                 qv1 >= lvv && qv1 < hvv;
                 if (__all_sync(0xffffffffu, in)) {
+                    // packed FP32x2 forms of the scalar arithmetic (each lane rounds as the scalar
+                    // instruction does, so the result is the same bit for bit): the two lerps along u
+                    // in one pair, and the (u, v) positions, or the v positions of two voxels, in another
                     const int bu = cfg.bu;
+                    const f32x2 M2 = splat2(12582912.0f);
                     if (V.flat) {
                         // u and w constant along the column
                         const float tu = __fadd_rd(qu0, 12582912.0f);
                         const float au = qu0 - (tu - 12582912.0f);
+                        const f32x2 au2 = splat2(au);
                         const T *bc = box + (__float_as_int(tu) - 0x4B400000 + du0);
                         const float om = W2 ? iw0 * iw0 : 1.0f;
+                        const f32x2 qb2 = splat2(V.Qb[2]), nb2 = splat2(nb), iw2 = splat2(iw0), fv2 = splat2(V.fv);
 #pragma unroll
-                        for (int z = 0; z < BZ; ++z) {
-                            const float qv = fmaf(fmaf((float)z, V.Qb[2], nb), iw0, V.fv);
-                            const float t = __fadd_rd(qv, 12582912.0f);
-                            const float av = qv - (t - 12582912.0f);
-                            const T *r = bc + (__float_as_int(t) - 0x4B400000 + dv0) * bu;
-                            const float q00 = to_f32(r[0]), q01 = to_f32(r[1]);
-                            const float q10 = to_f32(r[bu]), q11 = to_f32(r[bu + 1]);
-                            const float r0 = fmaf(au, q01 - q00, q00);
-                            const float r1 = fmaf(au, q11 - q10, q10);
-                            acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
+                        for (int z = 0; z < BZ; z += 2) {
+                            // voxels z and z + 1 (BZ is even)
+                            const f32x2 qv = fma2(fma2(pack2((float)z, (float)(z + 1)), qb2, nb2), iw2, fv2);
+                            const f32x2 t = add2_rd(qv, M2);
+                            const f32x2 av = sub2(qv, sub2(t, M2));
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const T *r = bc + (__float_as_int(h ? hi2(t) : lo2(t)) - 0x4B400000 + dv0) * bu;
+                                const f32x2 rr = lerp2(au2, pack2(to_f32(r[0]), to_f32(r[bu])),
+                                                       pack2(to_f32(r[1]), to_f32(r[bu + 1])));
+                                const float r0 = lo2(rr), r1 = hi2(rr);
+                                acc[z + h] = fmaf(om, fmaf(h ? hi2(av) : lo2(av), r1 - r0, r0), acc[z + h]);
+                            }
                         }
                     } else {
+                        const f32x2 qab2 = pack2(V.Qa[2], V.Qb[2]), nab2 = pack2(na, nb), fuv2 = pack2(V.fu, V.fv);
 #pragma unroll
                         for (int z = 0; z < BZ; ++z) {
                             const float fz = (float)z;
                             const float iw = rcp_fast(fmaf(fz, V.Pw[2], w));
-                            const float qu = fmaf(fmaf(fz, V.Qa[2], na), iw, V.fu);
-                            const float qv = fmaf(fmaf(fz, V.Qb[2], nb), iw, V.fv);
-                            const float tu = __fadd_rd(qu, 12582912.0f), tv = __fadd_rd(qv, 12582912.0f);
-                            const float au = qu - (tu - 12582912.0f), av = qv - (tv - 12582912.0f);
-                            const T *r = box + ((__float_as_int(tv) - 0x4B400000 + dv0) * bu +
-                                                (__float_as_int(tu) - 0x4B400000 + du0));
-                            const float q00 = to_f32(r[0]), q01 = to_f32(r[1]);
-                            const float q10 = to_f32(r[bu]), q11 = to_f32(r[bu + 1]);
-                            const float r0 = fmaf(au, q01 - q00, q00);
-                            const float r1 = fmaf(au, q11 - q10, q10);
+                            const f32x2 q = fma2(fma2(splat2(fz), qab2, nab2), splat2(iw), fuv2);   // (u, v)
+                            const f32x2 t = add2_rd(q, M2);
+                            const f32x2 a = sub2(q, sub2(t, M2));
+                            const T *r = box + ((__float_as_int(hi2(t)) - 0x4B400000 + dv0) * bu +
+                                                (__float_as_int(lo2(t)) - 0x4B400000 + du0));
+                            const f32x2 rr = lerp2(splat2(lo2(a)), pack2(to_f32(r[0]), to_f32(r[bu])),
+                                                   pack2(to_f32(r[1]), to_f32(r[bu + 1])));
+                            const float r0 = lo2(rr), r1 = hi2(rr);
                             const float om = W2 ? iw * iw : 1.0f;
-                            acc[z] = fmaf(om, fmaf(av, r1 - r0, r0), acc[z]);
+                            acc[z] = fmaf(om, fmaf(hi2(a), r1 - r0, r0), acc[z]);
                         }
                     }
                     continue;
