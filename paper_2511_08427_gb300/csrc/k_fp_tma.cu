@@ -40,7 +40,7 @@
 
 namespace pyronn {
 
-constexpr int TMA_TU = 16, TMA_TV = 16, TMA_NT = TMA_TU * TMA_TV;
+constexpr int TMA_TU = FP_TILE_U, TMA_TV = FP_TILE_V, TMA_NT = TMA_TU * TMA_TV;
 struct TmaMaps {
     CUtensorMap map[3];   // one box shape per march axis
 };

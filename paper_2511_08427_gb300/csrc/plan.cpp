@@ -192,7 +192,7 @@ int pyronn_plan_info(pyronn_plan_t P, int *n, int64_t *items_fp, int64_t *items_
     long long ifp = 0, ib = 0;
     for (int i = 0; i < P->n; ++i) {
         const pyronn_geom *g = P->geoms[i];
-        ifp += (long long)g->n_views * ((g->nu + 15) / 16) * ((g->nv + 15) / 16);
+        ifp += (long long)g->n_views * ((g->nu + FP_TILE_U - 1) / FP_TILE_U) * ((g->nv + FP_TILE_V - 1) / FP_TILE_V);
         ib += (long long)((g->nx + 15) / 16) * ((g->ny + 15) / 16) * ((g->nz + 15) / 16);
     }
     if (items_fp) *items_fp = ifp;
@@ -241,8 +241,8 @@ int pyronn_plan_fp(pyronn_plan_t P, const void *const *vols, void *const *sinos,
         V.in = vols[i];
         V.out = sinos[i];
         V.vt = V.cfg.xt ? (void *)(P->d_vt + P->vt_off[i]) : nullptr;
-        V.ntx = (g->nu + 15) / 16;
-        V.nty = (g->nv + 15) / 16;
+        V.ntx = (g->nu + FP_TILE_U - 1) / FP_TILE_U;
+        V.nty = (g->nv + FP_TILE_V - 1) / FP_TILE_V;
         V.ntz = 1;
         acc += (long long)g->n_views * V.ntx * V.nty;
         L.item_end[L.n++] = acc;

@@ -96,6 +96,10 @@ struct FpSlabCfg {
     int valid;             // 0: use the direct kernel
 };
 
+// Detector tile of one CTA of the TMA-staged forward projector (pixels along u, along v); a warp takes
+// 32 consecutive lanes: 16 x 2 pixels
+constexpr int FP_TILE_U = 16, FP_TILE_V = 16;
+
 // Box shapes of the TMA-staged forward projector (chosen per geometry and element size).
 struct FpTmaBox {
     int bx[3], by[3], bz[3];   // box extents (x, y, z) for march axis m = 0, 1, 2
