@@ -96,8 +96,8 @@ struct FpSlabCfg {
     int valid;             // 0: use the direct kernel
 };
 
-// Detector tile of one CTA of the TMA-staged forward projector (pixels along u, along v); a warp takes
-// 32 consecutive lanes: 16 x 2 pixels
+// Detector tile of one CTA of the TMA-staged forward projector (pixels along u, along v); the 32 lanes
+// of a warp take 16 x 2 of its pixels
 constexpr int FP_TILE_U = 16, FP_TILE_V = 16;
 
 // Box shapes of the TMA-staged forward projector (chosen per geometry and element size).
