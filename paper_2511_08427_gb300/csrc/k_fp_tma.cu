@@ -62,13 +62,17 @@ struct FpTmaShared {
 
 // One detector tile (tile_x, tile_y) of one view of volume b: returns false if a tensor copy was lost
 // (the CTA must stop). bars / ph: the CTA's two slab mbarriers and the number of loads already
-// consumed on each (the wait parity), carried across tiles by persistent launches.
-template <typename T>
+// consumed on each (the wait parity), carried across tiles by persistent launches. PK: the sample
+// loop's arithmetic (FpTmaBox::packed) fixed at compile time, so that a kernel holds one sample loop
+// (fewer live values, no spills in the loop), or -1 to read it from cfg (persistent launches, whose
+// volumes may differ).
+template <typename T, int PK>
 __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &cfg, const CUtensorMap *maps3,
                                             const T *__restrict__ vol, T *__restrict__ sino, int view, int b,
                                             int tile_x, int tile_y, T *const buf0, T *const buf1, FpTmaShared &sh,
                                             unsigned ph[2]) {
     const bool dbl = cfg.nbuf == 2;
+    const int pk = PK >= 0 ? PK : cfg.packed;
     float (*s_corner)[6] = sh.corner;
     int *s_srange = sh.srange;
     const int tu0 = tile_x * TMA_TU, tv0 = tile_y * TMA_TV;
@@ -274,7 +278,7 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 float v000 = 0.0f, v001 = 0.0f, v010 = 0.0f, v011 = 0.0f;
                 float v100 = 0.0f, v101 = 0.0f, v110 = 0.0f, v111 = 0.0f;
                 const float M = 12582912.0f;
-                const bool packed = cfg.packed != 0;   // 1: packed lerps; 2: packed lerps and positions
+                const bool packed = pk != 0;   // 1: packed lerps; 2: packed lerps and positions
                 auto sample = [&](int base, float ax, float ay, float az) {
                     if (base != pbase) {
                         const T *s0 = box + base;
@@ -312,7 +316,7 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 const float ex = (float)(BF - 1), ey = (float)(BS - 1), ez = (float)(BZb - 1);
                 if (qax >= 0.f && qbx >= 0.f && qax < ex && qbx < ex && qay >= 0.f && qby >= 0.f && qay < ey &&
                     qby < ey && qaz >= 0.f && qbz >= 0.f && qaz < ez && qbz < ez) {
-                    if (cfg.packed == 2) {
+                    if (pk == 2) {
                         // (x, y) positions, floors and fractions in FP32x2 lanes: the same roundings as
                         // the scalar loop below, in 5 instead of 9 operations per sample
                         const f32x2 st2 = pack2(stx, sty), c02 = pack2(c0x, c0y), M2 = splat2(M);
@@ -411,7 +415,7 @@ __device__ __forceinline__ void fp_tma_buffers(unsigned char *smem_raw, int buf_
 }
 
 // MINB: CTAs per SM the register allocation must allow (4 where four slab buffers fit in shared memory)
-template <typename T, int MINB>
+template <typename T, int MINB, int PK>
 __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_kernel(OpParams p, FpTmaBox cfg,
                                                            const __grid_constant__ TmaMaps maps,
                                                            const T *__restrict__ vol, T *__restrict__ sino) {
@@ -425,8 +429,8 @@ __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_kernel(OpParams p, FpTmaB
     // in consecutive views, whose rays cross the same band of the volume, so the band stays in L2 while
     // the resident CTAs read it (see the launcher)
     const int ntv = (p.det.nv + TMA_TV - 1) / TMA_TV;
-    fp_tma_tile<T>(p, cfg, maps.map, vol, sino, blockIdx.y, blockIdx.z / ntv, blockIdx.x, blockIdx.z % ntv, buf0,
-                   buf1, sh, ph);
+    fp_tma_tile<T, PK>(p, cfg, maps.map, vol, sino, blockIdx.y, blockIdx.z / ntv, blockIdx.x, blockIdx.z % ntv,
+                       buf0, buf1, sh, ph);
 }
 
 // Persistent launch over the (view, tile) items of several volumes: each CTA takes the next item
@@ -458,8 +462,8 @@ __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_batched_kernel(const __gr
         const int view = (int)(local / tiles), t = (int)(local % tiles);
         T *buf0, *buf1;
         fp_tma_buffers<T>(smem_raw, V.cfg.buf_elems, V.cfg.nbuf, buf0, buf1);
-        if (!fp_tma_tile<T>(V.p, V.cfg, M.map[i], (const T *)V.in, (T *)V.out, view, 0, t % V.ntx, t / V.ntx, buf0,
-                            buf1, sh, ph))
+        if (!fp_tma_tile<T, -1>(V.p, V.cfg, M.map[i], (const T *)V.in, (T *)V.out, view, 0, t % V.ntx, t / V.ntx,
+                                buf0, buf1, sh, ph))
             return;
     }
 }
@@ -653,7 +657,14 @@ static int launch_tma_t(const OpParams &p, const FpTmaBox &cfg, const void *vol,
                         cudaStream_t st, int make_copy) {
     if (cfg.xt && !vol_t) return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)cfg.nbuf * sizeof(T) * (size_t)cfg.buf_elems + 128;
-    auto kern = cfg.minb == 4 ? fp_tma_kernel<T, 4> : (cfg.minb == 3 ? fp_tma_kernel<T, 3> : fp_tma_kernel<T, 2>);
+    // one instantiation per (CTAs per SM, sample arithmetic)
+    void (*kern)(OpParams, FpTmaBox, TmaMaps, const T *, T *);
+    if (cfg.packed == 0)
+        kern = cfg.minb == 4 ? fp_tma_kernel<T, 4, 0> : (cfg.minb == 3 ? fp_tma_kernel<T, 3, 0> : fp_tma_kernel<T, 2, 0>);
+    else if (cfg.packed == 1)
+        kern = cfg.minb == 4 ? fp_tma_kernel<T, 4, 1> : (cfg.minb == 3 ? fp_tma_kernel<T, 3, 1> : fp_tma_kernel<T, 2, 1>);
+    else
+        kern = cfg.minb == 4 ? fp_tma_kernel<T, 4, 2> : (cfg.minb == 3 ? fp_tma_kernel<T, 3, 2> : fp_tma_kernel<T, 2, 2>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
