@@ -314,6 +314,17 @@ __device__ __forceinline__ void as_ray_dir(const AsTile &T, float fu, float fv, 
     dd[2] = fmaf(T.dref[2], g, L2 * inv);
 }
 
+// a[j] for a runtime j < AS_RPT by a chain of selects: every access to a[] has a constant index, so the
+// array stays in registers (a dynamically indexed array would live in local memory, whose loads miss
+// the small L1 left beside the slab boxes and wait on L2)
+template <typename V>
+__device__ __forceinline__ V as_pick(const V (&a)[AS_RPT], int j) {
+    V r = a[0];
+#pragma unroll
+    for (int i = 1; i < AS_RPT; ++i) r = j == i ? a[i] : r;
+    return r;
+}
+
 // Zeroes the box (box_cap floats); as_tile expects a zero box and leaves it zero.
 __device__ __forceinline__ void as_zero_box(float *box, int box_cap) {
     for (int e = 4 * threadIdx.x; e + 3 < box_cap; e += 4 * AS_NT)
@@ -323,13 +334,16 @@ __device__ __forceinline__ void as_zero_box(float *box, int box_cap) {
 
 // Detector tile (tile_x, tile_y) of one view of batch item b: adds y_scale A^T (sino - sino_b) (sino_b
 // may be null) into the FP32 volume vol.
-template <typename T>
+// CELL: the accumulation of fixed-point slabs fixed at compile time (AdjSlabCfg::cell_fixed: 0 one
+// reduction per sample and corner, 1 cell sums), so that the default kernel's cell loop serves FP32
+// boxes only; -1 reads it from cfg (persistent launches, whose volumes may differ).
+template <typename T, int CELL>
 __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg, const T *__restrict__ sino,
                                         const T *__restrict__ sino_b, float y_scale, float *__restrict__ vol,
                                         int view, int b, int tile_x, int tile_y, float *box, AsSlab *slabs,
                                         AsShared &sh) {
     const int depth = cfg.depth, guard = cfg.guard, box_cap = cfg.box_cap;
-    const int allow_fixed = cfg.allow_fixed, cell_fixed = cfg.cell_fixed;
+    const int allow_fixed = cfg.allow_fixed, cell_fixed = CELL >= 0 ? CELL : cfg.cell_fixed;
     const int tu0 = tile_x * AS_TU, tv0 = tile_y * AS_TV;
     const int tu1 = min(tu0 + AS_TU, p.det.nu) - 1, tv1 = min(tv0 + AS_TV, p.det.nv) - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -391,10 +405,10 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
             v = tv0 + warp * AS_RPT + j;
         }
     };
-    // per-ray state kept across slabs: value y dt (0: nothing to scatter), and the global FP32 ray's
-    // march-axis coordinate, inverse step and sample range, which define the slab partition
+    // per-ray state kept across slabs (in registers, read through as_pick): value y dt (0: nothing to
+    // scatter), and the global FP32 ray's march-axis coordinate, inverse step and sample range, which
+    // define the slab partition; the precise direction is formed again per slab (as_ray_dir)
     float yv[AS_RPT], rcm[AS_RPT], rinv[AS_RPT];
-    float rdir[AS_RPT][6];   // unit direction d and its change dd from the tile's corner ray (slab-independent)
     int rk0[AS_RPT], rk1[AS_RPT];
     unsigned ybits = 0u;
 #pragma unroll
@@ -440,12 +454,6 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         rcm[j] = cm;
         rinv[j] = 1.0f / (dt * dm);
         rk0[j] = k0;
-        {
-            float d[3], dd[3];
-            as_ray_dir(sh.tile, (float)(u - tu0), (float)(v - tv0), d, dd);
-            rdir[j][0] = d[0]; rdir[j][1] = d[1]; rdir[j][2] = d[2];
-            rdir[j][3] = dd[0]; rdir[j][4] = dd[1]; rdir[j][5] = dd[2];
-        }
         rk1[j] = k1;
         const float qa = fmaf(fmaf((float)k0, dt, 0.5f * dt), dm, cm);
         const float qb = fmaf(fmaf((float)k1, dt, 0.5f * dt), dm, cm);
@@ -561,12 +569,12 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         const int b_hi = min(b_lo + D, Nm);
 #pragma unroll 1
         for (int j = 0; j < AS_RPT; ++j) {
-            const float y = yv[j];
+            const float y = as_pick(yv, j);
             if (y == 0.0f) continue;   // rays outside the detector or the volume, zero values, direct rays
             int u, v;
             pixel(j, u, v);
             // slab partition on the global FP32 ray (identical formula for the shared boundaries)
-            const float cm = rcm[j], inv_step = rinv[j];
+            const float cm = as_pick(rcm, j), inv_step = as_pick(rinv, j);
             int ka, kb;
             if (inv_step > 0.0f) {
                 ka = (int)ceilf(fmaf((float)b_lo - cm, inv_step, -0.5f));
@@ -575,8 +583,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                 ka = (int)floorf(fmaf((float)b_hi - cm, inv_step, -0.5f)) + 1;
                 kb = (int)floorf(fmaf((float)b_lo - cm, inv_step, -0.5f));
             }
-            ka = max(ka, rk0[j]);
-            kb = min(kb, rk1[j]);
+            ka = max(ka, as_pick(rk0, j));
+            kb = min(kb, as_pick(rk1, j));
             if (ka > kb) continue;
             if (Ex == 0) {
                 as_scatter_global(p, vb, ray_setup(rec, p.vol, (float)u, (float)v), ka, kb, y);
@@ -585,8 +593,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
             // precise local ray: point P on the plane through X_s, unit direction d, and the offset e
             // of (X_s + P) . d from the phase T dt of the tile's corner ray (K + f = T)
             const float fu = (float)(u - tu0), fv = (float)(v - tv0);
-            const float d[3] = {rdir[j][0], rdir[j][1], rdir[j][2]};
-            const float dd[3] = {rdir[j][3], rdir[j][4], rdir[j][5]};
+            float d[3], dd[3];
+            as_ray_dir(sh.tile, fu, fv, d, dd);
             const float P0 = fmaf(fv, S.Ev[0], fmaf(fu, S.Eu[0], S.A[0]));
             const float P1 = fmaf(fv, S.Ev[1], fmaf(fu, S.Eu[1], S.A[1]));
             const float P2 = fmaf(fv, S.Ev[2], fmaf(fu, S.Eu[2], S.A[2]));
@@ -704,7 +712,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                     // the cell's 2 x 2 x 2 block lies in the box: eight reductions (corners outside the volume
                     // land in the box margin and are dropped when the box is added)
                     const unsigned a = box_base + 4u * (unsigned)pcell;
-                    if (fx) {
+                    if (CELL != 0 && fx) {   // fixed-point slabs reach this loop only in cell mode
                         as_red_shared_s32(a, __float2int_rn(a0));
                         as_red_shared_s32(a + 4u, __float2int_rn(a1v));
                         as_red_shared_s32(a + sy4, __float2int_rn(a2v));
@@ -807,7 +815,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
     }
 }
 
-template <typename T>
+template <typename T, int CELL>
 __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, AdjSlabCfg cfg, const T *__restrict__ sino,
                                                                 const T *__restrict__ sino_b, float y_scale,
                                                                 float *__restrict__ vol) {
@@ -818,8 +826,8 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_kernel(OpParams p, AdjS
     // grid (tile columns, views, tile rows x batch items), in the order that keeps the volume band of
     // one tile row in L2 while the resident CTAs reduce into it (see the launcher)
     const int ntv = (p.det.nv + AS_TV - 1) / AS_TV;
-    as_tile<T>(p, cfg, sino, sino_b, y_scale, vol, blockIdx.y, blockIdx.z / ntv, blockIdx.x, blockIdx.z % ntv, box,
-               slabs, sh);
+    as_tile<T, CELL>(p, cfg, sino, sino_b, y_scale, vol, blockIdx.y, blockIdx.z / ntv, blockIdx.x, blockIdx.z % ntv,
+                     box, slabs, sh);
 }
 
 // Persistent launch over the (view, tile) items of several volumes (each with its own geometry and
@@ -849,7 +857,7 @@ __global__ void __launch_bounds__(AS_NT, 2) adjoint_slab_batched_kernel(const __
         const long long local = item - (i ? L.item_end[i - 1] : 0);
         const int tiles = V.ntx * V.nty;
         const int view = (int)(local / tiles), t = (int)(local % tiles);
-        as_tile<T>(V.p, V.acfg, (const T *)V.in, (const T *)nullptr, 1.0f, V.acc, view, 0, t % V.ntx, t / V.ntx,
+        as_tile<T, -1>(V.p, V.acfg, (const T *)V.in, (const T *)nullptr, 1.0f, V.acc, view, 0, t % V.ntx, t / V.ntx,
                    box, slabs, sh);
     }
 }
@@ -1003,10 +1011,10 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
     else if ((void *)acc != vol) adjoint_widen_kernel<T><<<cblocks, 256, 0, st>>>((const T *)vol, acc, n);
     if (e != cudaSuccess) return (int)e;
     const size_t smem = adjoint_slab_smem_bytes(c.box_cap, c.max_slabs);
-    e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = c.cell_fixed ? adjoint_slab_kernel<T, 1> : adjoint_slab_kernel<T, 0>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(adjoint_slab_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     // Grid order: tile columns fastest, then views, then tile rows and batch items, so that the CTAs
     // resident at one time (the tiles of one tile row in consecutive views) reduce into one band of the
@@ -1027,7 +1035,7 @@ static int launch_slab_t(const OpParams &p, const AdjSlabCfg &c, const void *sin
             q.n_views = nvw;
             const long long so = b0 * p.sino_elems + v0 * view_elems;
             dim3 grid(ceil_div(p.det.nu, AS_TU), nvw, ntv * nb);
-            adjoint_slab_kernel<T><<<grid, AS_NT, smem, st>>>(
+            kern<<<grid, AS_NT, smem, st>>>(
                 q, c, (const T *)sino + so, sino_b ? (const T *)sino_b + so : (const T *)nullptr, y_scale,
                 acc + b0 * p.vol_elems);
         }
