@@ -52,12 +52,13 @@ struct SlabBox {
 
 constexpr int FP_RING = 16;   // slab boxes computed ahead, one per lane of warp 0
 
+template <bool RING>
 struct FpTmaShared {
     unsigned long long bar[2];
     float corner[5][6];
     int srange[2];
-    SlabBox box[2];         // boxes of the slabs in the two copy slots (written by the issuing thread)
-    SlabBox ring[FP_RING];  // boxes of the next slabs of the tile (warp 0 only)
+    SlabBox box[2];                   // boxes of the slabs in the two copy slots (written by the issuing thread)
+    SlabBox ring[RING ? FP_RING : 1]; // boxes of the next slabs of the tile (warp 0 only)
 };
 
 // One detector tile (tile_x, tile_y) of one view of volume b: returns false if a tensor copy was lost
@@ -65,11 +66,12 @@ struct FpTmaShared {
 // consumed on each (the wait parity), carried across tiles by persistent launches. PK: the sample
 // loop's arithmetic (FpTmaBox::packed) fixed at compile time, so that a kernel holds one sample loop
 // (fewer live values, no spills in the loop), or -1 to read it from cfg (persistent launches, whose
-// volumes may differ).
-template <typename T, int PK>
+// volumes may differ). RING: slab boxes computed ahead by warp 0 (below) or by thread 0 as it issues
+// each copy (the persistent launches, whose small volumes' tiles have few slabs, run faster that way).
+template <typename T, int PK, bool RING>
 __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &cfg, const CUtensorMap *maps3,
                                             const T *__restrict__ vol, T *__restrict__ sino, int view, int b,
-                                            int tile_x, int tile_y, T *const buf0, T *const buf1, FpTmaShared &sh,
+                                            int tile_x, int tile_y, T *const buf0, T *const buf1, FpTmaShared<RING> &sh,
                                             unsigned ph[2]) {
     const bool dbl = cfg.nbuf == 2;
     const int pk = PK >= 0 ? PK : cfg.packed;
@@ -200,12 +202,14 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
         __syncwarp();
     };
 
+    auto box_for = [&](int i) { return RING ? sh.ring[i % FP_RING] : slab_box(s_first + i); };
+
     float acc = 0.0f;
     const float hdt = 0.5f * p.dt;
     if (nsl > 0) {
-        if (tid < 32) fill_ring(0);
+        if (RING && tid < 32) fill_ring(0);
         if (tid == 0) {
-            const SlabBox sb0 = sh.ring[0];
+            const SlabBox sb0 = box_for(0);
             sh.box[0] = sb0;
             mbar_expect_tx(bars[0], box_bytes);
             tma_load_4d(smem_u32(buf0), tmap, bars[0], yt ? sb0.lo[1] : sb0.lo[0], yt ? sb0.lo[0] : sb0.lo[1],
@@ -215,10 +219,12 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
             const int s = s_first + i;
             const int bi = dbl ? (i & 1) : 0;
             const unsigned parity = ph[bi] & 1u;
-            if (dbl && tid < 32 && i + 1 < nsl) {
-                if ((i + 1) % FP_RING == 0) fill_ring(i + 1);
+            // issued by thread 0; with the ring the whole of warp 0 takes the block (its lanes refill the
+            // ring every FP_RING slabs), which measured faster than a separate refill branch
+            if (dbl && tid < (RING ? 32 : 1) && i + 1 < nsl) {
+                if (RING && (i + 1) % FP_RING == 0) fill_ring(i + 1);
                 if (tid == 0) {
-                    const SlabBox sbn = sh.ring[(i + 1) % FP_RING];
+                    const SlabBox sbn = box_for(i + 1);
                     sh.box[(i + 1) & 1] = sbn;
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_expect_tx(bars[bi ^ 1], box_bytes);
@@ -372,10 +378,11 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
                 }
             }
             __syncthreads();   // everyone is done with this buffer before it is refilled
-            if (!dbl && tid < 32 && i + 1 < nsl) {
-                if ((i + 1) % FP_RING == 0) fill_ring(i + 1);
+            // issued by thread 0, with warp 0 in the block where it refills the ring (as above)
+            if (!dbl && tid < (RING ? 32 : 1) && i + 1 < nsl) {
+                if (RING && (i + 1) % FP_RING == 0) fill_ring(i + 1);
                 if (tid == 0) {
-                    const SlabBox sbn = sh.ring[(i + 1) % FP_RING];
+                    const SlabBox sbn = box_for(i + 1);
                     sh.box[(i + 1) & 1] = sbn;
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_expect_tx(bars[0], box_bytes);
@@ -397,7 +404,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
     return true;
 }
 
-__device__ __forceinline__ void fp_tma_init_bars(FpTmaShared &sh) {
+template <bool RING>
+__device__ __forceinline__ void fp_tma_init_bars(FpTmaShared<RING> &sh) {
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&sh.bar[0]), 1);
         mbar_init(smem_u32(&sh.bar[1]), 1);
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_kernel(OpParams p, FpTmaB
                                                            const __grid_constant__ TmaMaps maps,
                                                            const T *__restrict__ vol, T *__restrict__ sino) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ FpTmaShared sh;
+    __shared__ FpTmaShared<true> sh;
     T *buf0, *buf1;
     fp_tma_buffers<T>(smem_raw, cfg.buf_elems, cfg.nbuf, buf0, buf1);
     fp_tma_init_bars(sh);
@@ -429,7 +437,7 @@ __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_kernel(OpParams p, FpTmaB
     // in consecutive views, whose rays cross the same band of the volume, so the band stays in L2 while
     // the resident CTAs read it (see the launcher)
     const int ntv = (p.det.nv + TMA_TV - 1) / TMA_TV;
-    fp_tma_tile<T, PK>(p, cfg, maps.map, vol, sino, blockIdx.y, blockIdx.z / ntv, blockIdx.x, blockIdx.z % ntv,
+    fp_tma_tile<T, PK, true>(p, cfg, maps.map, vol, sino, blockIdx.y, blockIdx.z / ntv, blockIdx.x, blockIdx.z % ntv,
                        buf0, buf1, sh, ph);
 }
 
@@ -439,11 +447,11 @@ struct PlanMaps {
     CUtensorMap map[PLAN_MAX][3];
 };
 
-template <typename T, int MINB>
+template <typename T, int MINB, int PK>
 __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_batched_kernel(const __grid_constant__ PlanLaunch L,
                                                                    const __grid_constant__ PlanMaps M) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ FpTmaShared sh;
+    __shared__ FpTmaShared<false> sh;
     __shared__ int s_item;
     fp_tma_init_bars(sh);
     unsigned ph[2] = {0u, 0u};
@@ -462,7 +470,7 @@ __global__ void __launch_bounds__(TMA_NT, MINB) fp_tma_batched_kernel(const __gr
         const int view = (int)(local / tiles), t = (int)(local % tiles);
         T *buf0, *buf1;
         fp_tma_buffers<T>(smem_raw, V.cfg.buf_elems, V.cfg.nbuf, buf0, buf1);
-        if (!fp_tma_tile<T, -1>(V.p, V.cfg, M.map[i], (const T *)V.in, (T *)V.out, view, 0, t % V.ntx, t / V.ntx,
+        if (!fp_tma_tile<T, PK, false>(V.p, V.cfg, M.map[i], (const T *)V.in, (T *)V.out, view, 0, t % V.ntx, t / V.ntx,
                                 buf0, buf1, sh, ph))
             return;
     }
@@ -711,7 +719,13 @@ static bool batched_four(size_t smem) { return 4 * (smem + 512 + 1024) <= 228 * 
 
 template <typename T>
 static int launch_batched_t(const PlanLaunch &L, int grid, size_t smem, cudaStream_t st) {
-    auto kern = batched_four(smem) ? fp_tma_batched_kernel<T, 4> : fp_tma_batched_kernel<T, 2>;
+    // the default sample arithmetic compiled in where every volume of the plan uses it (one sample loop
+    // per kernel), else read per volume
+    bool all2 = true;
+    for (int i = 0; i < L.n; ++i) all2 = all2 && L.v[i].cfg.packed == 2;
+    void (*kern)(PlanLaunch, PlanMaps);
+    if (all2) kern = batched_four(smem) ? fp_tma_batched_kernel<T, 4, 2> : fp_tma_batched_kernel<T, 2, 2>;
+    else kern = batched_four(smem) ? fp_tma_batched_kernel<T, 4, -1> : fp_tma_batched_kernel<T, 2, -1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
@@ -747,7 +761,7 @@ int launch_fp_tma_batched(const PlanLaunch &L, int dtype, int grid, size_t smem,
 
 template <typename T>
 static int batched_occupancy_t(size_t smem, int *blocks_per_sm) {
-    auto kern = batched_four(smem) ? fp_tma_batched_kernel<T, 4> : fp_tma_batched_kernel<T, 2>;
+    auto kern = batched_four(smem) ? fp_tma_batched_kernel<T, 4, 2> : fp_tma_batched_kernel<T, 2, 2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
