@@ -562,7 +562,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         const bool fx = S.scale != 0.0f;
         const float ysc = fx ? S.scale : 1.0f;
         const bool per_sample = fx && !cell_fixed;
-        const int lo0 = S.lo[0], lo1 = S.lo[1], lo2 = S.lo[2];
+        const int bo0 = S.lo[0], bo1 = S.lo[1], bo2 = S.lo[2];   // box origin
         const int Px = S.px;
         const unsigned sy4 = 4u * (unsigned)Px, sz4 = 4u * (unsigned)(Px * Ey);
         const int b_lo = base0 + s * D;
@@ -626,33 +626,48 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                     // constant is folded into the box base address (unsigned arithmetic mod 2^32)
                     const float Mg = 12582912.0f;
                     const unsigned abase = box_base - 0x4B400000u * (sz4 + sy4 + 4u);
-                    auto sample = [&](float jj) {
-                        const float sj = fmaf(jj, dt, c_r);
-                        const float q0 = fmaf(sj, qd0, qP0), q1 = fmaf(sj, qd1, qP1), q2 = fmaf(sj, qd2, qP2);
-                        const float t0 = __fadd_rd(q0, Mg), t1 = __fadd_rd(q1, Mg), t2 = __fadd_rd(q2, Mg);
-                        const float ax = q0 - (t0 - Mg), ay = q1 - (t1 - Mg), az = q2 - (t2 - Mg);
-                        const unsigned a = abase + 4u * __float_as_uint(t0) + sy4 * __float_as_uint(t1) +
+                    // Packed FP32x2 forms of the scalar arithmetic (each lane rounds as the scalar instruction
+                    // does, so the contributions are the same bit for bit): the (x, y) positions, floors and
+                    // fractions in one pair, the weights of the two y rows, and the contributions of the y
+                    // pairs of corners, rounded by the magic-number FFMA.
+                    const f32x2 M2 = splat2(Mg), dt2 = splat2(dt), cr2 = splat2(c_r);
+                    const f32x2 qd01 = pack2(qd0, qd1), qP01 = pack2(qP0, qP1);
+                    auto fix_bits = [](float c) { return (int)(__float_as_uint(c) - 0x4B400000u); };
+                    auto sample = [&](f32x2 jj2) {   // jj2 = (jj, jj)
+                        const f32x2 sj2 = fma2(jj2, dt2, cr2);
+                        const f32x2 q01 = fma2(sj2, qd01, qP01);
+                        const float q2 = fmaf(lo2(sj2), qd2, qP2);
+                        const f32x2 t01 = add2_rd(q01, M2);
+                        const float t2 = __fadd_rd(q2, Mg);
+                        const f32x2 a01 = sub2(q01, sub2(t01, M2));   // (ax, ay)
+                        const float az = q2 - (t2 - Mg);
+                        const unsigned a = abase + 4u * __float_as_uint(lo2(t01)) + sy4 * __float_as_uint(hi2(t01)) +
                                            sz4 * __float_as_uint(t2);
                         const float wz1 = ys * az, wz0 = ys - wz1;
-                        const float oay = 1.f - ay, oax = 1.f - ax;
-                        const float w00 = wz0 * oay, w01 = wz0 * ay, w10 = wz1 * oay, w11 = wz1 * ay;
-                        as_red_shared_s32(a, as_fix(w00, oax));
-                        as_red_shared_s32(a + 4u, as_fix(w00, ax));
-                        as_red_shared_s32(a + sy4, as_fix(w01, oax));
-                        as_red_shared_s32(a + sy4 + 4u, as_fix(w01, ax));
-                        as_red_shared_s32(a + sz4, as_fix(w10, oax));
-                        as_red_shared_s32(a + sz4 + 4u, as_fix(w10, ax));
-                        as_red_shared_s32(a + sz4 + sy4, as_fix(w11, oax));
-                        as_red_shared_s32(a + sz4 + sy4 + 4u, as_fix(w11, ax));
+                        const float ax = lo2(a01), ay = hi2(a01);
+                        const f32x2 yy = pack2(1.f - ay, ay);
+                        const f32x2 w0 = mul2(splat2(wz0), yy), w1 = mul2(splat2(wz1), yy);   // (w00, w01), (w10, w11)
+                        const f32x2 ox = splat2(1.f - ax), xx = splat2(ax);
+                        const f32x2 c0 = fma2(w0, ox, M2), c1 = fma2(w0, xx, M2);
+                        const f32x2 c2 = fma2(w1, ox, M2), c3 = fma2(w1, xx, M2);
+                        as_red_shared_s32(a, fix_bits(lo2(c0)));
+                        as_red_shared_s32(a + 4u, fix_bits(lo2(c1)));
+                        as_red_shared_s32(a + sy4, fix_bits(hi2(c0)));
+                        as_red_shared_s32(a + sy4 + 4u, fix_bits(hi2(c1)));
+                        as_red_shared_s32(a + sz4, fix_bits(lo2(c2)));
+                        as_red_shared_s32(a + sz4 + 4u, fix_bits(lo2(c3)));
+                        as_red_shared_s32(a + sz4 + sy4, fix_bits(hi2(c2)));
+                        as_red_shared_s32(a + sz4 + sy4 + 4u, fix_bits(hi2(c3)));
                     };
                     // two independent samples per step
-                    float jj = jf;
+                    f32x2 jj2 = splat2(jf);
+                    const f32x2 one2 = splat2(1.0f), two2 = splat2(2.0f);
                     int ii = 0;
-                    for (; ii + 1 < n; ii += 2, jj += 2.0f) {
-                        sample(jj);
-                        sample(jj + 1.0f);
+                    for (; ii + 1 < n; ii += 2, jj2 = add2(jj2, two2)) {
+                        sample(jj2);
+                        sample(add2(jj2, one2));
                     }
-                    if (ii < n) sample(jj);
+                    if (ii < n) sample(jj2);
                     continue;
                 }
                 float jj = jf;
@@ -680,7 +695,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                     } else {
                         const float vals[8] = {w00 * oax, w00 * ax, w01 * oax, w01 * ax,
                                                w10 * oax, w10 * ax, w11 * oax, w11 * ax};
-                        as_out_of_box(p, vb, ix + lo0, iy + lo1, iz + lo2, vals, isc);
+                        as_out_of_box(p, vb, ix + bo0, iy + bo1, iz + bo2, vals, isc);
                     }
                 }
                 continue;
@@ -740,7 +755,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                 if (off_box) {
                     const float vals[8] = {w00 * (1.f - ax), w00 * ax, w01 * (1.f - ax), w01 * ax,
                                            w10 * (1.f - ax), w10 * ax, w11 * (1.f - ax), w11 * ax};
-                    as_out_of_box(p, vb, ix + lo0, iy + lo1, iz + lo2, vals, fx ? isc : 1.0f);
+                    as_out_of_box(p, vb, ix + bo0, iy + bo1, iz + bo2, vals, fx ? isc : 1.0f);
                     continue;
                 }
                 a0 = fmaf(w00, 1.f - ax, a0);
@@ -782,7 +797,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
                     if (fx)
                         q = make_float4(__int2float_rn(qi.x) * isc, __int2float_rn(qi.y) * isc,
                                         __int2float_rn(qi.z) * isc, __int2float_rn(qi.w) * isc);
-                    const int gx = lo0 + 4 * xg, gy = lo1 + ly, gz = lo2 + lz;
+                    const int gx = bo0 + 4 * xg, gy = bo1 + ly, gz = bo2 + lz;
                     if ((unsigned)gy < (unsigned)p.vol.ny && (unsigned)gz < (unsigned)p.vol.nz) {
                         // 32-bit index: volumes hold fewer than 2^31 voxels (gx may be slightly negative)
                         float *dst = vb + ((gz * p.vol.ny + gy) * p.vol.nx + gx);
