@@ -295,8 +295,10 @@ __device__ void as_tile_setup(const OpParams &p, int view, int u0, int v0, AsTil
 }
 
 // Ray (u0 + du, v0 + dv) of the tile: unit direction d and its change from the corner ray dd
-// (formed without cancellation, as in the brick adjoint).
-__device__ __forceinline__ void as_ray_dir(const AsTile &T, float fu, float fv, float d[3], float dd[3]) {
+// (formed without cancellation, as in the brick adjoint). as_ray_norm forms the ray's two scalars (the
+// normalisation inv and the correction g: the divisions and the square root), as_ray_dir the vectors
+// from them.
+__device__ __forceinline__ void as_ray_norm(const AsTile &T, float fu, float fv, float &inv, float &g) {
     const float L0 = fmaf(fv, T.Cv[0], fu * T.Cu[0]);
     const float L1 = fmaf(fv, T.Cv[1], fu * T.Cu[1]);
     const float L2 = fmaf(fv, T.Cv[2], fu * T.Cu[2]);
@@ -304,11 +306,18 @@ __device__ __forceinline__ void as_ray_dir(const AsTile &T, float fu, float fv, 
     const float LL = fmaf(L0, L0, fmaf(L1, L1, L2 * L2));
     const float eps = (2.0f * DL + LL) / T.nD2;
     const float sq = sqrtf(1.0f + eps);
-    const float inv = T.inv_nD / sq;
+    inv = T.inv_nD / sq;
+    g = -eps / (sq * (1.0f + sq));
+}
+
+__device__ __forceinline__ void as_ray_dir(const AsTile &T, float fu, float fv, float inv, float g, float d[3],
+                                           float dd[3]) {
+    const float L0 = fmaf(fv, T.Cv[0], fu * T.Cu[0]);
+    const float L1 = fmaf(fv, T.Cv[1], fu * T.Cu[1]);
+    const float L2 = fmaf(fv, T.Cv[2], fu * T.Cu[2]);
     d[0] = (T.D[0] + L0) * inv;
     d[1] = (T.D[1] + L1) * inv;
     d[2] = (T.D[2] + L2) * inv;
-    const float g = -eps / (sq * (1.0f + sq));
     dd[0] = fmaf(T.dref[0], g, L0 * inv);
     dd[1] = fmaf(T.dref[1], g, L1 * inv);
     dd[2] = fmaf(T.dref[2], g, L2 * inv);
@@ -407,8 +416,9 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
     };
     // per-ray state kept across slabs (in registers, read through as_pick): value y dt (0: nothing to
     // scatter), and the global FP32 ray's march-axis coordinate, inverse step and sample range, which
-    // define the slab partition; the precise direction is formed again per slab (as_ray_dir)
-    float yv[AS_RPT], rcm[AS_RPT], rinv[AS_RPT];
+    // define the slab partition; the precise direction is formed again per slab (as_ray_dir) from the
+    // ray's normalisation scalars
+    float yv[AS_RPT], rcm[AS_RPT], rinv[AS_RPT], rnrm[AS_RPT], rgc[AS_RPT];
     int rk0[AS_RPT], rk1[AS_RPT];
     unsigned ybits = 0u;
 #pragma unroll
@@ -425,6 +435,8 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         ybits = max(ybits, __float_as_uint(fabsf(yv[j])));
         rcm[j] = 0.0f;
         rinv[j] = 0.0f;
+        rnrm[j] = 0.0f;
+        rgc[j] = 0.0f;
         rk0[j] = 0;
         rk1[j] = -1;
     }
@@ -455,6 +467,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
         rinv[j] = 1.0f / (dt * dm);
         rk0[j] = k0;
         rk1[j] = k1;
+        as_ray_norm(sh.tile, (float)(u - tu0), (float)(v - tv0), rnrm[j], rgc[j]);
         const float qa = fmaf(fmaf((float)k0, dt, 0.5f * dt), dm, cm);
         const float qb = fmaf(fmaf((float)k1, dt, 0.5f * dt), dm, cm);
         const float qlo = fmaxf(fminf(qa, qb), -1.0f), qhi = fminf(fmaxf(qa, qb), (float)Nm);
@@ -594,7 +607,7 @@ __device__ __forceinline__ void as_tile(const OpParams &p, const AdjSlabCfg &cfg
             // of (X_s + P) . d from the phase T dt of the tile's corner ray (K + f = T)
             const float fu = (float)(u - tu0), fv = (float)(v - tv0);
             float d[3], dd[3];
-            as_ray_dir(sh.tile, fu, fv, d, dd);
+            as_ray_dir(sh.tile, fu, fv, as_pick(rnrm, j), as_pick(rgc, j), d, dd);
             const float P0 = fmaf(fv, S.Ev[0], fmaf(fu, S.Eu[0], S.A[0]));
             const float P1 = fmaf(fv, S.Ev[1], fmaf(fu, S.Eu[1], S.A[1]));
             const float P2 = fmaf(fv, S.Ev[2], fmaf(fu, S.Eu[2], S.A[2]));
