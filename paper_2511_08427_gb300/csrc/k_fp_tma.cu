@@ -4,10 +4,12 @@
 // planes along the tile's dominant axis m, exact sample partition through integer slab
 // boundaries), but the slab box is moved by the Tensor Memory Accelerator: one thread issues a
 // cp.async.bulk.tensor load of a fixed-size box (chosen on the host as the largest footprint of
-// any tile), the hardware zero-fills everything outside the volume, and two buffers let the load
-// of slab s + 1 run under the sampling of slab s. Completion is tracked by mbarrier transaction
-// counts; every wait is bounded, and a CTA whose copy does not arrive sets an error counter and
-// leaves.
+// any tile), the hardware zero-fills everything outside the volume, and two buffers (where they fit
+// beside the other CTAs of an SM; the autotuner usually prefers one deeper buffer) let the load of
+// slab s + 1 run under the sampling of slab s. The slabs' box origins are computed ahead by the lanes
+// of warp 0, sixteen slabs at a time, so that a copy is issued right after the barrier that frees its
+// buffer. Completion is tracked by mbarrier transaction counts; every wait is bounded, and a CTA whose
+// copy does not arrive sets an error counter and leaves.
 //
 // Sample loop: positions relative to the box origin, floor / fraction by the round-down
 // magic-number addition (no conversion-pipe instructions), eight shared-memory reads, seven
@@ -152,7 +154,8 @@ __device__ __forceinline__ bool fp_tma_tile(const OpParams &p, const FpTmaBox &c
     const unsigned bars[2] = {smem_u32(&sh.bar[0]), smem_u32(&sh.bar[1])};
     const int align = 16 / (int)sizeof(T);
 
-    // box of slab s, computed by the thread that issues the slab's copy and shared through sh.box
+    // box of slab s (origin and whether the tile's footprint fits), from the corner rays' crossings of the
+    // slab's end planes; the issuing thread shares it with the CTA through sh.box
     auto slab_box = [&](int s) {
         SlabBox sb;
         const int b_lo = base0 + s * D;
