@@ -509,3 +509,18 @@ def test_views_match_oracle_over_random_geometries(L):
         assert g.kind == og.kind, it
         assert np.allclose(g.views(), og.views, rtol=1e-12, atol=1e-12), it
         assert abs(g.step - og.dt) < 1e-15, it
+
+
+def test_projector_automatic_depth_by_storage_type(L):
+    """The TMA projector's automatic slab depth: 8 planes for FP32, 16 for 2-byte storage where four CTAs
+    still share an SM (its boxes are half the bytes); an explicit depth is kept for every type."""
+    import torch
+    from paper_2511_08427_gb300.operators import TUNE_FP_DEPTH, Geometry
+    g = Geometry.cone_circular((64, 96, 128), (0.5, 0.5, 0.5), (96, 128), (0.6, 0.6), 40, 2 * math.pi, 750.0, 1200.0)
+    assert g.fp_config(torch.float32)["depth"] == 8
+    for td in (torch.bfloat16, torch.float16):
+        c = g.fp_config(td)
+        assert c["kernel"] == 3 and c["depth"] == 16
+        assert 4 * (c["smem_bytes"] + 512 + 1024) <= 228 * 1024
+    g.set_tuning(TUNE_FP_DEPTH, 8)
+    assert g.fp_config(torch.bfloat16)["depth"] == 8 and g.fp_config(torch.float32)["depth"] == 8
