@@ -564,12 +564,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn() {
 // the row pitch is not a multiple of 16 bytes). xt: x-march boxes may come from a y-fastest copy of
 // the volume (taken where its rows, ny elements, are a multiple of 16 bytes too).
 FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbuf, int minb, int xt) {
-    // automatic depth for 2-byte storage: 16 planes where four CTAs still share an SM (the boxes are
-    // half the bytes, and the deeper slab repays the per-operand conversion: 44.6 against 49.4 ms on the
-    // 256^3 workload, 963 against 1064 ms on the 512^3 one), else 8 as for FP32
-    if (depth == 0 && elem == 2) {
-        const FpTmaBox c16 = choose_fp_tma_box(g, elem, 16, nbuf, minb, xt);
-        if (c16.depth > 0 && c16.minb == 4) return c16;
+    // automatic depth: the deeper slab where four CTAs still share an SM (fewer slab boundaries and copy
+    // waits per ray), else 8 planes: 12 for FP32 (896 against 954 ms on the 512^3 workload; on the 256^3
+    // one its box is too wide for four CTAs), 16 for 2-byte storage, whose boxes are half the bytes and
+    // whose per-operand conversion the deeper slab repays (44.6 against 49.4 ms on the 256^3 workload, 963
+    // against 1064 ms on the 512^3 one)
+    if (depth == 0 && (elem == 2 || elem == 4)) {
+        const FpTmaBox cd = choose_fp_tma_box(g, elem, elem == 2 ? 16 : 12, nbuf, minb, xt);
+        if (cd.depth > 0 && cd.minb == 4) return cd;
     }
     FpTmaBox c{};
     const int align = 16 / (int)elem;

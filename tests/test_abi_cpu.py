@@ -512,12 +512,13 @@ def test_views_match_oracle_over_random_geometries(L):
 
 
 def test_projector_automatic_depth_by_storage_type(L):
-    """The TMA projector's automatic slab depth: 8 planes for FP32, 16 for 2-byte storage where four CTAs
-    still share an SM (its boxes are half the bytes); an explicit depth is kept for every type."""
+    """The TMA projector's automatic slab depth: 12 planes for FP32 and 16 for 2-byte storage where four
+    CTAs still share an SM (else 8); an explicit depth is kept for every type."""
     import torch
     from paper_2511_08427_gb300.operators import TUNE_FP_DEPTH, Geometry
     g = Geometry.cone_circular((64, 96, 128), (0.5, 0.5, 0.5), (96, 128), (0.6, 0.6), 40, 2 * math.pi, 750.0, 1200.0)
-    assert g.fp_config(torch.float32)["depth"] == 8
+    c = g.fp_config(torch.float32)
+    assert c["kernel"] == 3 and c["depth"] == 12 and 4 * (c["smem_bytes"] + 512 + 1024) <= 228 * 1024
     for td in (torch.bfloat16, torch.float16):
         c = g.fp_config(td)
         assert c["kernel"] == 3 and c["depth"] == 16
