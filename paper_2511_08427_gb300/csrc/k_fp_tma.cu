@@ -610,7 +610,9 @@ FpTmaBox choose_fp_tma_box(const pyronn_geom *g, size_t elem, int depth, int nbu
     for (int m = 0; m < 3; ++m) {
         int e[3];
         for (int a = 0; a < 3; ++a) {
-            if (a == m) e[a] = std::min(c.depth + 2 * c.guard + 1, dims[a] + 2 * c.guard + 2);
+            // along m a slab's box spans planes b_lo - guard .. min(b_lo + depth, N) + guard, and the first
+            // slab starts at slab0 (at or below plane -1)
+            if (a == m) e[a] = std::min(c.depth + 2 * c.guard + 1, dims[a] - c.slab0 + 2 * c.guard + 1);
             else e[a] = (int)ext[m][a];
             if (a != m && e[a] == 0) e[a] = 1;   // axis never chosen: keep a valid box
         }
