@@ -769,3 +769,21 @@ def test_packed_interpolation_is_bit_identical(ops, case, dtype):
     for mode in (2, 3):
         g.set_tuning(ops.TUNE_FP_PACKED, mode)
         assert torch.equal(ops.forward_project(x, g), scalar), mode
+
+
+@pytest.mark.parametrize("depth", [12, 16, 24])
+@pytest.mark.parametrize("name", ["helical", "jittered_positions"])
+def test_projector_slabs_deeper_than_the_volume(ops, name, depth):
+    """TMA projector slabs deeper than the volume along the march axis (the first slab starts below plane
+    -1 at an x-aligned plane, so its box spans more than N + 2 guard + 2 planes): every slab fits its
+    box (no overflow flag) and the projection matches the oracle."""
+    case = next(c for c in SMALL if c.name == name)
+    g = case.library_geometry()
+    g.set_tuning(ops.TUNE_FP_DEPTH, depth)
+    assert g.fp_config()["kernel"] == 3
+    og = case.oracle_geometry()
+    x = case.phantom()
+    g.read_flags(reset=True)
+    p = host(ops.forward_project(to_dev(x), g))
+    assert rel_l2(p, oracle.fp(og, x)) <= 1e-5
+    assert g.read_flags()[:4] == [0, 0, 0, 0]
